@@ -1,0 +1,188 @@
+/*
+ * hz.h -- C ABI of the GB300 three-grid IOFD Helmholtz library (libhz.so).
+ *
+ * The library solves the PML-truncated Helmholtz problem
+ *     -sum_j xi_j^-1 d_j (xi_j^-1 d_j u) - k(x)^2 u = f,  u = 0 on the box boundary
+ * (Sec. 2.1, Eq. helmholtz-pml) with the compact 27-point IOFD discretisation
+ * P_h v = Q_h f, u = Q_h v (Sec. 2.2, Eq. iofd-complete-system), by FGMRES
+ * right-preconditioned with the three-grid cycle of Algorithm 1 (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: nx, ny, nz intervals per axis INCLUDING n_pml PML layers on each
+ *     side; (nx+1)(ny+1)(nz+1) nodal unknowns (Sec. 5, "an n^3 mesh has
+ *     (n+1)^3 nodal unknowns").  nx, ny, nz and n_pml must be divisible by 4
+ *     (two coarsenings, each halving the PML layers, Sec. 3.1).
+ *   - Field layout: x fastest, then y, then z; for nrhs right-hand sides the
+ *     fields are stacked, [rhs][z][y][x].  Complex values are interleaved
+ *     (re, im): complex64 = 2 x float, complex128 = 2 x double.
+ *   - Level L in {0, 1, 2} is the grid of spacing 2^L h (h, 2h, 4h), with
+ *     (nx/2^L + 1)(ny/2^L + 1)(nz/2^L + 1) nodes.
+ *   - Pointers named *_dev are DEVICE pointers on the handle's device;
+ *     pointers named *_host are host pointers.  The caller owns every buffer
+ *     it passes; the library never frees or retains them past the call.
+ *     Input and output buffers must not alias unless stated.
+ *   - `stream` arguments are cudaStream_t values (0 = legacy default stream)
+ *     passed as void*; work is enqueued on it and the call returns without
+ *     synchronising unless stated.
+ *   - Every entry point returns an hz_status; on failure hz_last_error()
+ *     gives a message.  No C++ exception crosses the ABI.  Calls on one
+ *     handle must not run concurrently from several host threads.
+ */
+#ifndef HZ_H_
+#define HZ_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_EINVAL = 1,      /* bad argument (null pointer, size, divisibility, range) */
+  HZ_ENOMEM = 2,      /* device allocation failed */
+  HZ_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  HZ_ENOCONV = 4,     /* max_pc reached before the tolerance (results are filled) */
+  HZ_ETIMEOUT = 5,    /* reserved: a bounded device wait gave up */
+  HZ_ENONFINITE = 6   /* a NaN/Inf appeared in a residual norm */
+} hz_status;
+
+/* precision of a call */
+enum { HZ_C64 = 0, HZ_C128 = 1 };
+
+/* operators for iofd_apply */
+enum {
+  HZ_OP_A = 0,      /* A_ell = L_ell - M_ell            (Eq. physical-iofd-levels)   */
+  HZ_OP_B = 1,      /* B_ell = L_ell - (1+i sigma) M_ell (Eq. shifted-iofd-levels)   */
+  HZ_OP_Q = 2,      /* Q_h amplitude correction, level 0 only (Eq. q-operator)       */
+  HZ_OP_A_ADJ = 3,  /* A_ell^H                                                        */
+  HZ_OP_B_ADJ = 4,  /* B_ell^H                                                        */
+  HZ_OP_Q_ADJ = 5   /* Q_h^H, level 0 only                                            */
+};
+
+typedef struct {
+  int nx, ny, nz;      /* intervals per axis, PML included */
+  int n_pml;           /* PML layers per side on the fine grid */
+  double h;            /* fine spacing */
+  double omega;        /* angular frequency (time dependence exp(-i omega t)) */
+  double gamma_max;    /* PML stretch amplitude (Eq. pml-profile); Table 4: 1.119058 */
+} hz_grid;
+
+typedef struct {
+  int ix, iy, iz;      /* source node */
+  double amp_re, amp_im;  /* f_h = amp h^-3 delta_{i,i_s} (Eq. point-source) */
+} hz_source;
+
+/* Solver configuration; hz_default_params() fills Table 4 of the paper
+ * (tol 1e-4 there; BASELINE workloads use 1e-6). */
+typedef struct {
+  double tol;          /* stop when ||A v - b|| / ||b|| <= tol (Eq. relative-residual) */
+  int max_pc;          /* cap on preconditioner calls (outer FGMRES steps) */
+  int m_out;           /* outer FGMRES restart length */
+  int m_h, nJ_h;       /* fine smoother: GMRES(m_h) right-preconditioned by nJ_h Jacobi sweeps */
+  int c_2h, m_2h;      /* 2h solve: c_2h FGMRES(m_2h) cycles on A_2h */
+  int nJ_2h;           /* Jacobi sweeps of the shifted 2h cycle */
+  int m_4h, nJ_4h;     /* 4h bottom: m_4h CA-GMRES steps, nJ_4h Jacobi sweeps */
+  double w_h, w_2h, w_4h;  /* Jacobi weights */
+  double sigma;        /* complex shift of B_2h, B_4h */
+  int precision;       /* HZ_C64: complex64 hierarchy and inner solves, FP64 outer
+                          Krylov scalars and FP64 iterative refinement;
+                          HZ_C128: everything in complex128 */
+  double inner_tol;    /* HZ_C64 only: floor of the relative tolerance of each
+                          complex64 correction solve inside the refinement loop */
+  int max_refine;      /* HZ_C64 only: cap on refinement passes */
+} hz_params;
+
+typedef struct {
+  int pc_calls;        /* preconditioner calls = outer FGMRES steps, all passes */
+  int refine_passes;   /* FP64 true-residual evaluations (HZ_C64) */
+  double rel_res;      /* final ||A v - b|| / ||b||, max over right-hand sides */
+  double t_setup;      /* seconds, per-level coefficients and tables */
+  double t_solve;      /* seconds */
+  size_t device_bytes; /* device memory held by the handle */
+} hz_stats;
+
+typedef struct hz_handle hz_handle;
+
+/* Table 4 defaults (Sec. 6.1): m_out 5, m_h 2 / nJ_h 2 / w_h 0.8, c_2h 2,
+ * m_2h 10, nJ_2h 2 / w_2h 0.8, m_4h 4 / nJ_4h 2 / w_4h 0.2, sigma 0.9,
+ * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8. */
+void hz_default_params(hz_params* p);
+
+/* Create a solver for one frequency and velocity model.
+ *   c_dev       DEVICE, double, (nx+1)(ny+1)(nz+1) wave speeds on every fine
+ *               node; values inside the PML are ignored and replaced by the
+ *               nearest physical value (Sec. 2.1).  Read during the call only.
+ *   table_host  HOST, double, table_rows x 17 IOFD Hermite data, one row per
+ *               uniform node s_k on [0, 0.4]: s, alpha_1..5, d alpha_1..5/ds,
+ *               beta_1..3, d beta_1..3/ds (Sec. 2.2: alpha_j, beta_j are cubic
+ *               Hermite interpolants of tabulated values).  2 <= rows <= 33.
+ *   max_nrhs    largest nrhs any later call will use (sizes the workspaces).
+ *   stream      stream for set-up work; the call synchronises it.
+ * Returns HZ_EINVAL for bad sizes, HZ_ENOMEM if the workspaces do not fit. */
+hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* params, const double* table_host,
+                    int table_rows, int max_nrhs, void* stream, hz_handle** out);
+hz_status hz_destroy(hz_handle* h);
+const char* hz_last_error(const hz_handle* h);
+/* Device bytes hz_create would allocate for these sizes. */
+hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int max_nrhs, size_t* bytes);
+/* Replace the solver parameters (e.g. tolerance); cached CUDA graphs are dropped. */
+hz_status hz_set_params(hz_handle* h, const hz_params* params);
+
+/* Per-level coefficients, for inspection (Eq. iofd-clamped-coordinate,
+ * Eq. iofd-shell-coefficients).
+ *   kappa_dev  DEVICE double, N_L values: kappa_{L,i} = k(x_i) 2^L h.
+ *   shell_dev  DEVICE double, 4 N_L values or NULL: the interior shell
+ *              coefficients C_0..C_3 of A_L at each node (times ell^2, as in
+ *              the paper), laid out [m][node].  Synchronises the handle stream. */
+hz_status iofd_coeffs(hz_handle* h, int level, double* kappa_dev, double* shell_dev);
+
+/* y = Op x on level `level` for nrhs stacked fields (Sec. 2.2 and Sec. 3.1).
+ *   x_dev, y_dev  DEVICE, complex64 (precision HZ_C64) or complex128, N_L*nrhs.
+ * HZ_OP_Q / HZ_OP_Q_ADJ require level 0.  1 <= nrhs <= max_nrhs. */
+hz_status iofd_apply(hz_handle* h, int level, int op, int precision, const void* x_dev, void* y_dev, int nrhs,
+                     void* stream);
+
+/* z = M_h^{-1} r: one application of the three-grid preconditioner of
+ * Algorithm 1 (pre-smooth S_h(r;0), restrict r - A_h z_pre, K_2h, prolong and
+ * correct, post-smooth S_h(r; z~)), with the shifted 2h-4h cycle of
+ * Eq. shifted-auxiliary-cycle inside K_2h (Eq. unshifted-middle-solve).
+ * Every inner method does its fixed work; the map depends on r nonlinearly.
+ *   r_dev, z_dev  DEVICE fine-grid fields (N_0 * nrhs) in `precision`.
+ *   adjoint       nonzero: the same structure built from A^H, B^H (used by
+ *                 the adjoint solve of the gradient).
+ * The call is enqueued as one CUDA graph launch on `stream`. */
+hz_status threegrid_precond(hz_handle* h, const void* r_dev, void* z_dev, int nrhs, int adjoint, int precision,
+                            void* stream);
+
+/* Solve A_h v = Q_h f for nsrc point sources (zero initial guess) with
+ * FGMRES(m_out) right-preconditioned by Algorithm 1 until
+ * ||A v - b|| / ||b|| <= tol for every source (Sec. 3.3, Eq. relative-residual).
+ *   src_host   HOST, nsrc sources; solved in groups of at most max_nrhs.
+ *   v_dev      DEVICE complex128, N_0 * nsrc: the IOFD auxiliary field v.
+ *   u_dev      DEVICE complex128, N_0 * nsrc, or NULL: the pressure u = Q_h v.
+ *   stats      HOST or NULL.
+ * Synchronises.  Returns HZ_ENOCONV (with v, u filled) if max_pc is reached. */
+hz_status helmholtz_solve(hz_handle* h, const hz_source* src_host, int nsrc, void* v_dev, void* u_dev,
+                          hz_stats* stats);
+
+/* Receiver misfit J = 1/2 sum_s || R Q_h v_s - d_s ||^2 and its gradient
+ * with respect to the squared slowness m = 1/c^2 on every fine node, by the
+ * adjoint-state method (forward solves, A^H lambda = Q^H R^T (R u - d),
+ * row-local derivatives of A_h and Q_h).  The PML copies the nearest physical
+ * velocity, so PML entries of the gradient are 0 and their contributions are
+ * added to that physical node.  (Not in the paper; its Sec. 1 motivates many
+ * sources for imaging and inversion.)
+ *   rec_host   HOST int, nrec x 3 node indices (ix, iy, iz), distinct.
+ *   dobs_host  HOST double, nsrc x nrec complex values (re, im interleaved).
+ *   misfit     HOST double out.
+ *   grad_dev   DEVICE double, N_0 values out.
+ * Synchronises. */
+hz_status helmholtz_adjoint_grad(hz_handle* h, const hz_source* src_host, int nsrc, const int* rec_host, int nrec,
+                                 const double* dobs_host, double* misfit, double* grad_dev, hz_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H_ */

@@ -1,0 +1,134 @@
+// Host-side launch interface of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "hz_common.cuh"
+
+namespace hz {
+
+enum StencilMode { M_APPLY = 0, M_RESID = 1, M_J2 = 2, M_JSWEEP = 3, M_J1 = 4 };
+enum StencilOp { OP_AB = 0, OP_Q = 1 };
+
+// Reduction target of a kernel that finishes with a deterministic
+// grid-wide sum: per-block partials, an arrival counter per group and the
+// output slot per group (all device memory owned by the handle).
+struct Reduce {
+  double* partial = nullptr;
+  unsigned* count = nullptr;
+  double* out = nullptr;       // sum per group
+  double* root = nullptr;      // optional sqrt(sum)
+  double* inv_root = nullptr;  // optional 1/sqrt(sum) (0 when the sum is 0)
+};
+
+template <class R>
+struct StencilCall {
+  LevelView<R> lv;
+  TableView<R> tab;
+  cx<R> mass_shift;      // 1 + i sigma (B) or 1 (A)
+  R omega_j = 0;         // Jacobi weight
+  const cx<R>* x = nullptr;     // APPLY/RESID: x; J2/J1: g; JSWEEP: current iterate y
+  const cx<R>* g = nullptr;     // RESID/JSWEEP: right-hand side
+  const cx<R>* base = nullptr;  // J2: out = base + J2(g) when non-null
+  cx<R>* y = nullptr;
+  int nrhs = 1;
+  Reduce red;            // RESID: ||y||^2 per rhs when red.out != nullptr
+};
+
+template <class R>
+void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s);
+
+// Grid transfers (Eq. full-weighting, Eq. linear-prolongation).
+template <class R>
+void launch_restrict(const cx<R>* fine, cx<R>* coarse, int nxf, int nyf, int nzf, int nrhs, cudaStream_t s);
+template <class R>
+void launch_prolong_add(const cx<R>* coarse, const cx<R>* base, cx<R>* fine, int nxf, int nyf, int nzf, int nrhs,
+                        cudaStream_t s);
+
+// Krylov vector passes.  Vectors of one basis are `vstride` elements apart;
+// each holds nrhs contiguous fields of n elements.  Scalars are complex
+// double pairs per rhs, rows of length `ld`.
+struct KrylovCall {
+  int n = 0;            // elements per field
+  int nrhs = 1;
+  long long vstride = 0;  // elements between basis vectors
+  int kn = 0;            // number of basis vectors involved
+  int ld = 0;            // leading dimension of per-rhs scalar rows (complex entries)
+};
+
+// w -= sum_k coef[r][k] V_k  (optional), then dots[r][k] = <V_k, w> (optional),
+// nrm2[r] = ||w||^2 (optional).  Results written by the last block, which
+// then runs `epi` (see hz_vec.cu).
+enum CgsEpi { EPI_STORE = 0, EPI_ARNOLDI_FIRST = 1, EPI_ARNOLDI_SECOND = 2, EPI_NORMALISE = 3 };
+template <class R>
+void launch_cgs(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coef, bool update, bool dots,
+                bool norm, double* dots_out, double* nrm_out, int epi, double* H, int col, double* scale_out,
+                double* beta_out, const Reduce& red, cudaStream_t s);
+
+// out = w * scale[r]  (scale real double per rhs)
+template <class R>
+void launch_scale(const cx<R>* w, cx<R>* out, const double* scale, int n, int nrhs, cudaStream_t s);
+
+// x = (x0 ? x0 : 0) + sum_k y[r][k] Z_k  (y complex double, rows of length ld)
+template <class R>
+void launch_combine(const cx<R>* Z, long long zstride, int kn, const double* y, int ld, const cx<R>* x0, cx<R>* x,
+                    int n, int nrhs, cudaStream_t s);
+
+// Small least-squares min || beta e1 - H y || per rhs (H: (m+1) x m, column-major
+// complex double, leading dim m+1, per rhs stride (m+1)*m); y rows of length ld.
+void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s);
+
+// Gram matrix of kn vectors, Cholesky, and the CA-GMRES least-squares solve
+// min || p_0 - sum_{k>=1} y_{k-1} p_k ||; writes y (kn-1 entries per rhs).
+template <class R>
+void launch_gram_lsq(const cx<R>* P, long long pstride, int kn, int n, int nrhs, double* y, int ld,
+                     const Reduce& red, cudaStream_t s);
+
+// y = a*x + b*y style helpers
+template <class R>
+void launch_axpy(const cx<R>* x, cx<R>* y, double ar, double ai, long long n, cudaStream_t s);
+template <class R>
+void launch_copy(const cx<R>* x, cx<R>* y, long long n, cudaStream_t s);
+template <class R>
+void launch_zero(cx<R>* y, long long n, cudaStream_t s);
+
+// Mixed precision glue.
+void launch_c128_to_c64_scaled(const cx<double>* in, cx<float>* out, const double* scale, int n, int nrhs,
+                               cudaStream_t s);
+void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const double* scale, int n, int nrhs,
+                                   cudaStream_t s);
+template <class R>
+void launch_norm2(const cx<R>* v, int n, int nrhs, const Reduce& red, cudaStream_t s);
+
+// Set-up: kappa_L[j] = omega * ell / c_ext[2^L j] with c extended into the PML
+// by its nearest physical value (Sec. 2.1, Sec. 3.1).
+template <class R>
+void launch_setup_kappa(const double* c, int nxf, int nyf, int nzf, int n_pml, int stride, double omega,
+                        double ell, R* kappa, cudaStream_t s);
+
+// Point sources f = h^-3 amp delta (Eq. point-source) written into zeroed fields.
+template <class R>
+void launch_point_sources(const int* idx3, const double* amp, int nsrc, int nx, int ny, int nz, double scale,
+                          cx<R>* f, cudaStream_t s);
+
+// Adjoint-state gradient (row-local derivatives of A and Q w.r.t. m = 1/c^2):
+// g_ext[i] += sum_r Re[ conj(lam_i) (dQ_i f - dA_i v) + conj(rres_i) dQ_i v ].
+void launch_gradient(const LevelView<double>& lv, const TableView<double>& tab, double omega_h,
+                     const cx<double>* v, const cx<double>* lam, const cx<double>* f, const cx<double>* rres,
+                     int nrhs, double* g_ext, cudaStream_t s);
+// g[t] = sum of g_ext over the nodes whose velocity copies physical node t
+// (identity inside, rays into the PML at its faces, edges and corners); 0 in the PML.
+void launch_fold_pml(const double* g_ext, double* g, int nx, int ny, int nz, int n_pml, cudaStream_t s);
+// Interior shell coefficients C_0..C_3 of A at every node (Eq. iofd-shell-coefficients), [m][node].
+void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& tab, double* out, cudaStream_t s);
+// Set kernel attributes once per process/device (dynamic shared memory opt-in).
+void init_kernel_attributes();
+
+// Receivers
+template <class R>
+void launch_gather(const cx<R>* u, const int* rec, int nrec, int n, int nrhs, cx<double>* out, cudaStream_t s);
+template <class R>
+void launch_scatter(const cx<double>* vals, const int* rec, int nrec, int n, int nrhs, cx<R>* out, cudaStream_t s);
+
+}  // namespace hz

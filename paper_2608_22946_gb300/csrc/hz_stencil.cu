@@ -1,0 +1,652 @@
+// 27-point IOFD stencil kernels for sm_103a.
+//
+// Operator (paper Sec. 2.2, Eq. iofd-shell-form / Eq. pml-second-difference):
+//   (H x)_i = -ell^-2 sum_j [ abar_j S_j + achk_j D_j ] - s kappa_i^2 ell^-2 (M x)_i
+// where, with the transverse weights a4, a5/4, (1-a4-a5)/4 of the row i,
+//   T_j(s)  = transverse-weighted sum of x over the plane at offset s along j,
+//   S_j     = T_j(+1) + T_j(-1) - 2 T_j(0),   D_j = T_j(+1) - T_j(-1),
+//   M x     = a1 N0 + a2/6 N1 + a3/12 N2 + (1-a1-a2-a3)/8 N3 (shell sums N_m),
+//   abar_j, achk_j = half sum / half difference of the two PML second-
+//   difference weights of row i along j (1 and 0 outside the PML),
+//   s = 1 (A_ell) or 1 + i sigma (B_ell, Eq. shifted-iofd-levels).
+// Coefficients are evaluated per row from kappa = k ell through the cubic
+// Hermite tables at eta* = min(kappa / 2 pi, 0.4) (Eq. iofd-clamped-coordinate).
+//
+// Forward kernel design: a CTA owns a 32 x 8 column tile and marches in z over
+// a block of planes.  Planes (tile + 1-node halo) stream into a 4-deep shared
+// memory ring with cp.async (zero-filled outside the grid, which imposes
+// u = 0).  Each thread reduces the 3x3 in-plane neighbourhood of its column
+// to a few partial sums once per plane and keeps three planes of partials in
+// registers, so every input value is read from shared memory a handful of
+// times instead of 27.  Tiles whose columns are all outside the x/y PML use
+// the 3-partial shell path; the others the 8-partial tensor-product path.
+// Epilogues fuse the residual (with its norm), the two-sweep Jacobi map from
+// zero (Eq. jacobi-map, n_J = 2) and one further Jacobi sweep.
+//
+// The adjoint kernel applies (H^H x)_i = sum_delta conj(H_{i+delta}(-delta)) x_{i+delta};
+// it needs the neighbours' own coefficients, which it evaluates once per
+// loaded node into shared memory.
+#include <algorithm>
+#include <cstdio>
+
+#include "hz_kernels.h"
+
+namespace hz {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int PW = TX + 2, PH = TY + 2, PLANE = PW * PH;
+constexpr int NSTAGE = 4;
+
+// ----------------------------------------------------------------------------
+// cp.async (zero fill when pred is false; the source address is then unused)
+// ----------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool pred) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  int sz = pred ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES), "r"(sz));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// ----------------------------------------------------------------------------
+// per-plane partial sums of the 3x3 in-plane neighbourhood
+// ----------------------------------------------------------------------------
+template <class R, bool GEN> struct Part;
+template <class R> struct Part<R, false> { cx<R> c, e, k; };
+template <class R> struct Part<R, true> { cx<R> c, ex, ey, k, gx, gy, kx, ky; };
+
+template <class R>
+__device__ __forceinline__ void zero_part(Part<R, false>& o) {
+  o.c = o.e = o.k = mkc<R>(0, 0);
+}
+template <class R>
+__device__ __forceinline__ void zero_part(Part<R, true>& o) {
+  o.c = o.ex = o.ey = o.k = o.gx = o.gy = o.kx = o.ky = mkc<R>(0, 0);
+}
+
+template <class R>
+__device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R, false>& o) {
+  const cx<R>* r0 = P + (ly - 1) * PW + lx;
+  const cx<R>* r1 = r0 + PW;
+  const cx<R>* r2 = r1 + PW;
+  cx<R> m0 = r0[-1], c0 = r0[0], p0 = r0[1];
+  cx<R> m1 = r1[-1], c1 = r1[0], p1 = r1[1];
+  cx<R> m2 = r2[-1], c2 = r2[0], p2 = r2[1];
+  o.c = c1;
+  o.e = (m1 + p1) + (c0 + c2);
+  o.k = (m0 + p0) + (m2 + p2);
+}
+template <class R>
+__device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R, true>& o) {
+  const cx<R>* r0 = P + (ly - 1) * PW + lx;
+  const cx<R>* r1 = r0 + PW;
+  const cx<R>* r2 = r1 + PW;
+  cx<R> m0 = r0[-1], c0 = r0[0], p0 = r0[1];
+  cx<R> m1 = r1[-1], c1 = r1[0], p1 = r1[1];
+  cx<R> m2 = r2[-1], c2 = r2[0], p2 = r2[1];
+  o.c = c1;
+  o.ex = m1 + p1;
+  o.ey = c0 + c2;
+  o.k = (m0 + p0) + (m2 + p2);
+  o.gx = p1 - m1;
+  o.gy = c2 - c0;
+  o.kx = (p0 + p2) - (m0 + m2);
+  o.ky = (m2 + p2) - (m0 + p0);
+}
+
+// ----------------------------------------------------------------------------
+// row application from three planes of partials
+// ----------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ cx<R> stiff_mass(const Part<R, false>& m, const Part<R, false>& o, const Part<R, false>& p,
+                                            const R* a, cx<R> abz, cx<R> acz, cx<R>& Mv) {
+  const R a1 = a[0], a2 = a[1], a3 = a[2], a4 = a[3], a5 = a[4];
+  const R q5 = a5 * (R)0.25, qb = ((R)1 - a4 - a5) * (R)0.25;
+  const R w1 = a2 * (R)(1.0 / 6.0), w2 = a3 * (R)(1.0 / 12.0), w3 = ((R)1 - a1 - a2 - a3) * (R)0.125;
+  cx<R> T3m = a4 * m.c + q5 * m.e + qb * m.k;
+  cx<R> T30 = a4 * o.c + q5 * o.e + qb * o.k;
+  cx<R> T3p = a4 * p.c + q5 * p.e + qb * p.k;
+  cx<R> S3 = (T3p + T3m) - (R)2 * T30;
+  cx<R> D3 = T3p - T3m;
+  cx<R> S12 = a4 * (o.e - (R)4 * o.c) + q5 * ((R)2 * (o.k - o.e)) + q5 * ((m.e + p.e) - (R)4 * (m.c + p.c)) +
+              qb * ((R)2 * ((m.k + p.k) - (m.e + p.e)));
+  Mv = a1 * o.c + w1 * (o.e + m.c + p.c) + w2 * (o.k + m.e + p.e) + w3 * (m.k + p.k);
+  return S12 + abz * S3 + acz * D3;
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> stiff_mass(const Part<R, true>& m, const Part<R, true>& o, const Part<R, true>& p,
+                                            const R* a, cx<R> abx, cx<R> acx, cx<R> aby, cx<R> acy, cx<R> abz,
+                                            cx<R> acz, cx<R>& Mv) {
+  const R a1 = a[0], a2 = a[1], a3 = a[2], a4 = a[3], a5 = a[4];
+  const R q5 = a5 * (R)0.25, qb = ((R)1 - a4 - a5) * (R)0.25;
+  const R w1 = a2 * (R)(1.0 / 6.0), w2 = a3 * (R)(1.0 / 12.0), w3 = ((R)1 - a1 - a2 - a3) * (R)0.125;
+  cx<R> T3m = a4 * m.c + q5 * (m.ex + m.ey) + qb * m.k;
+  cx<R> T30 = a4 * o.c + q5 * (o.ex + o.ey) + qb * o.k;
+  cx<R> T3p = a4 * p.c + q5 * (p.ex + p.ey) + qb * p.k;
+  cx<R> S3 = (T3p + T3m) - (R)2 * T30;
+  cx<R> D3 = T3p - T3m;
+  cx<R> S1 = a4 * (o.ex - (R)2 * o.c) + q5 * (o.k - (R)2 * o.ey) + q5 * ((m.ex + p.ex) - (R)2 * (m.c + p.c)) +
+             qb * ((m.k + p.k) - (R)2 * (m.ey + p.ey));
+  cx<R> S2 = a4 * (o.ey - (R)2 * o.c) + q5 * (o.k - (R)2 * o.ex) + q5 * ((m.ey + p.ey) - (R)2 * (m.c + p.c)) +
+             qb * ((m.k + p.k) - (R)2 * (m.ex + p.ex));
+  cx<R> D1 = a4 * o.gx + q5 * o.kx + q5 * (m.gx + p.gx) + qb * (m.kx + p.kx);
+  cx<R> D2 = a4 * o.gy + q5 * o.ky + q5 * (m.gy + p.gy) + qb * (m.ky + p.ky);
+  Mv = a1 * o.c + w1 * (o.ex + o.ey + m.c + p.c) + w2 * (o.k + m.ex + m.ey + p.ex + p.ey) + w3 * (m.k + p.k);
+  return abx * S1 + acx * D1 + aby * S2 + acy * D2 + abz * S3 + acz * D3;
+}
+
+// Q_h row (Eq. q-operator) from the shell partials.
+template <class R>
+__device__ __forceinline__ cx<R> q_row(const Part<R, false>& m, const Part<R, false>& o, const Part<R, false>& p,
+                                       const R* b) {
+  const R q0 = b[0], q1 = b[1] * (R)(1.0 / 6.0), q2 = b[2] * (R)(1.0 / 12.0);
+  const R q3 = ((R)1 - b[0] - b[1] - b[2]) * (R)0.125;
+  return q0 * o.c + q1 * (o.e + m.c + p.c) + q2 * (o.k + m.e + p.e) + q3 * (m.k + p.k);
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> ldc(const cx<R>* p) { return *p; }
+
+// ----------------------------------------------------------------------------
+// forward kernel body
+// ----------------------------------------------------------------------------
+template <class R, int MODE, int OP, bool GEN>
+__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, int tiles_x, cx<R> (*sX)[PLANE],
+                                         R (*sK)[PLANE], cx<R>* sY1, const R* sTab, double* sRed) {
+  const LevelView<R>& L = a.lv;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int rhs = blockIdx.x % a.nrhs, tile_x = blockIdx.x / a.nrhs;
+  const int x0 = tile_x * TX, y0 = blockIdx.y * TY;
+  const int zb0 = blockIdx.z * zblock;
+  const int zb1 = min(zb0 + zblock, L.nz);
+  const int nplanes = zb1 - zb0 + 2;
+  const long long N = L.N;
+  const cx<R>* X = a.x + rhs * N;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = (gx < L.nx) && (gy < L.ny);
+  const long long col = (long long)gy * L.nx + gx;
+  const long long plane_sz = (long long)L.nx * L.ny;
+  const R inv_ell2 = L.inv_ell2;
+  const cx<R> shift = a.mass_shift;
+  const int nseg = a.tab.nseg;
+  const R ds = a.tab.ds, inv_ds = a.tab.inv_ds;
+
+  // per-thread PML factors of its column (x, y fixed during the march)
+  cx<R> abx = mkc<R>(1, 0), acx = mkc<R>(0, 0), aby = mkc<R>(1, 0), acy = mkc<R>(0, 0);
+  if (GEN && OP == OP_AB) {
+    int cxi = min(gx, L.nx - 1), cyi = min(gy, L.ny - 1);
+    abx = L.abar[0][cxi];
+    acx = L.achk[0][cxi];
+    aby = L.abar[1][cyi];
+    acy = L.achk[1][cyi];
+  }
+
+  auto issue = [&](int z, int st) {
+    for (int i = tid; i < PLANE; i += NT) {
+      int ly = i / PW, lx = i - ly * PW;
+      int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
+      bool in = (z >= 0) && (z < L.nz) && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
+      long long off = in ? ((long long)z * plane_sz + (long long)qy * L.nx + qx) : 0;
+      cp_async<sizeof(cx<R>)>(&sX[st][i], X + off, in);
+      if (MODE == M_J2) cp_async<sizeof(R)>(&sK[st][i], L.kappa + off, in);
+    }
+    cp_commit();
+  };
+
+  // prologue: planes 0, 1, 2 of the block (zb0-1 .. zb0+1)
+  for (int k = 0; k < 3; ++k) {
+    if (k < nplanes) issue(zb0 - 1 + k, k);
+    else cp_commit();
+  }
+
+  Part<R, GEN> wm, w0, wp;
+  zero_part(wm);
+  zero_part(w0);
+  R kap_prev = 0, kap_cur = 0;
+  cx<R> g_prev = mkc<R>(0, 0), g_cur = mkc<R>(0, 0);      // RESID/JSWEEP rhs, J2 raw g
+  cx<R> xc_prev = mkc<R>(0, 0), xc_cur = mkc<R>(0, 0);    // JSWEEP iterate / J2 y1 at centre
+  cx<R> dinv_prev = mkc<R>(0, 0), dinv_cur = mkc<R>(0, 0);
+  double nrm2 = 0.0;
+  const cx<R>* G = (MODE == M_RESID || MODE == M_JSWEEP) ? a.g + rhs * N : nullptr;
+
+  for (int k = 0; k < nplanes; ++k) {
+    const int zk = zb0 - 1 + k;
+    const int st = k % NSTAGE;
+    cp_wait<2>();
+    __syncthreads();
+    {
+      int kk = k + 3;
+      if (kk < nplanes) issue(zb0 - 1 + kk, kk % NSTAGE);
+      else cp_commit();
+    }
+    const bool zin = (zk >= 0) && (zk < L.nz);
+    const cx<R>* P = sX[st];
+    if (MODE == M_J2) {
+      // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first sweep)
+      cx<R> abz = zin ? L.abar[2][zk] : mkc<R>(1, 0);
+      for (int e = tid; e < PLANE; e += NT) {
+        // element e < NT is the thread's own column, the rest the halo ring
+        int lx, ly;
+        if (e < NT) {
+          lx = tx + 1;
+          ly = ty + 1;
+        } else {
+          int hsel = e - NT;  // 0 .. 2*PW + 2*TY - 1
+          if (hsel < PW) { lx = hsel; ly = 0; }
+          else if (hsel < 2 * PW) { lx = hsel - PW; ly = PH - 1; }
+          else if (hsel < 2 * PW + TY) { lx = 0; ly = hsel - 2 * PW + 1; }
+          else { lx = PW - 1; ly = hsel - 2 * PW - TY + 1; }
+        }
+        int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
+        int li = ly * PW + lx;
+        bool in = zin && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
+        cx<R> y1 = mkc<R>(0, 0), dinv = mkc<R>(0, 0);
+        cx<R> g = P[li];
+        R kap = sK[st][li];
+        if (in) {
+          R av[5];
+          table_eval<R, 0, 5>(sTab, nseg, ds, inv_ds, eta_star(kap), av);
+          cx<R> sab = L.abar[0][qx] + L.abar[1][qy] + abz;
+          cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (inv_ell2 * kap * kap * av[0]) * shift;
+          dinv = cinv(D);
+          y1 = a.omega_j * (dinv * g);
+        }
+        sY1[li] = y1;
+        if (e < NT) {
+          g_cur = g;
+          kap_cur = kap;
+          dinv_cur = dinv;
+          xc_cur = y1;
+        }
+      }
+      __syncthreads();
+      P = sY1;
+    } else {
+      if (active && zin) {
+        long long idx = (long long)zk * plane_sz + col;
+        kap_cur = L.kappa[idx];
+        if (MODE == M_RESID || MODE == M_JSWEEP) g_cur = G[idx];
+        if (MODE == M_JSWEEP) xc_cur = P[(ty + 1) * PW + tx + 1];
+      }
+    }
+    partials(P, tx + 1, ty + 1, wp);
+
+    if (k >= 2 && active) {
+      const int z = zk - 1;
+      const long long idx = (long long)z * plane_sz + col;
+      cx<R> out;
+      if (OP == OP_Q) {
+        R bv[3];
+        table_eval<R, 5, 3>(sTab, nseg, ds, inv_ds, eta_star(kap_prev), bv);
+        if constexpr (!GEN) out = q_row(wm, w0, wp, bv);
+        else out = mkc<R>(0, 0);
+      } else {
+        R av[5];
+        table_eval<R, 0, 5>(sTab, nseg, ds, inv_ds, eta_star(kap_prev), av);
+        cx<R> abz = L.abar[2][z], acz = L.achk[2][z];
+        cx<R> Mv, Ls;
+        if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, abx, acx, aby, acy, abz, acz, Mv);
+        else Ls = stiff_mass(wm, w0, wp, av, abz, acz, Mv);
+        const R mk = inv_ell2 * kap_prev * kap_prev;
+        cx<R> Hx = (-inv_ell2) * Ls - (mk * shift) * Mv;
+        if (MODE == M_APPLY) {
+          out = Hx;
+        } else if (MODE == M_RESID) {
+          out = g_prev - Hx;
+        } else if (MODE == M_J2) {
+          out = xc_prev + a.omega_j * (dinv_prev * (g_prev - Hx));
+          if (a.base) out += a.base[rhs * N + idx];
+        } else {  // M_JSWEEP
+          cx<R> sab = abx + aby + abz;
+          cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (mk * av[0]) * shift;
+          out = xc_prev + a.omega_j * cdiv(g_prev - Hx, D);
+        }
+      }
+      a.y[rhs * N + idx] = out;
+      if (MODE == M_RESID) nrm2 += (double)abs2(out);
+    }
+    wm = w0;
+    w0 = wp;
+    kap_prev = kap_cur;
+    g_prev = g_cur;
+    xc_prev = xc_cur;
+    dinv_prev = dinv_cur;
+  }
+  cp_wait<0>();
+
+  if (MODE == M_RESID && a.red.out) {
+    double s = block_sum(nrm2, sRed, tid, NT);
+    const unsigned nblk = (unsigned)(tiles_x * gridDim.y * gridDim.z);
+    const unsigned bid = (unsigned)(tile_x + tiles_x * (blockIdx.y + gridDim.y * blockIdx.z));
+    if (tid == 0) a.red.partial[(size_t)rhs * nblk + bid] = s;
+    if (last_block_arrive(a.red.count + rhs, nblk, tid)) {
+      double t = 0.0;
+      for (unsigned b = tid; b < nblk; b += NT) t += __ldcg(a.red.partial + (size_t)rhs * nblk + b);
+      // fixed-order combine: per-thread strided sums then the block tree
+      t = block_sum(t, sRed, tid, NT);
+      if (tid == 0) {
+        a.red.out[rhs] = t;
+        if (a.red.root) a.red.root[rhs] = sqrt(t);
+        if (a.red.inv_root) a.red.inv_root[rhs] = t > 1e-300 ? 1.0 / sqrt(t) : 0.0;
+        a.red.count[rhs] = 0;
+      }
+    }
+  }
+}
+
+template <class R, int MODE, int OP>
+__global__ void __launch_bounds__(NT) k_fwd(StencilCall<R> a, int zblock, int tiles_x) {
+  __shared__ cx<R> sX[NSTAGE][PLANE];
+  __shared__ R sK[NSTAGE][(MODE == M_J2) ? PLANE : 1];
+  __shared__ cx<R> sY1[(MODE == M_J2) ? PLANE : 1];
+  __shared__ R sTab[kMaxSeg * kNumFn * 4];
+  __shared__ double sRed[32];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (int i = tid; i < a.tab.nseg * kNumFn * 4; i += NT) sTab[i] = a.tab.coef[i];
+  // (visibility of sTab is ensured by the first __syncthreads of the march)
+  const LevelView<R>& L = a.lv;
+  const int tile_x = blockIdx.x / a.nrhs;
+  const int x0 = tile_x * TX, y0 = blockIdx.y * TY;
+  const bool plain = (OP == OP_Q) || ((x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) &&
+                                      (y0 >= L.plain_lo[1]) && (y0 + TY - 1 <= L.plain_hi[1]));
+  R(*sKp)[PLANE] = reinterpret_cast<R(*)[PLANE]>(&sK[0][0]);  // only dereferenced in M_J2
+  if constexpr (OP == OP_Q) {
+    fwd_body<R, MODE, OP, false>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
+  } else {
+    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
+    else fwd_body<R, MODE, OP, true>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// adjoint kernel: generic 27-neighbour gather with neighbour coefficients
+// ----------------------------------------------------------------------------
+template <int OP> struct AdjNP { static constexpr int v = 8; };
+template <> struct AdjNP<OP_Q> { static constexpr int v = 4; };
+
+template <class R, int MODE, int OP>
+__global__ void __launch_bounds__(NT) k_adj(StencilCall<R> a, int zblock, int tiles_x) {
+  constexpr int NP = AdjNP<OP>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* sV = reinterpret_cast<cx<R>*>(smem_raw);            // [3][PLANE]
+  R* sP = reinterpret_cast<R*>(sV + 3 * PLANE);                // [3][PLANE][NP]
+  R* sTab = sP + 3 * PLANE * NP;                               // table
+  __shared__ double sRed[32];
+  const LevelView<R>& L = a.lv;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  for (int i = tid; i < a.tab.nseg * kNumFn * 4; i += NT) sTab[i] = a.tab.coef[i];
+  __syncthreads();
+  const int rhs = blockIdx.x % a.nrhs, tile_x = blockIdx.x / a.nrhs;
+  const int x0 = tile_x * TX, y0 = blockIdx.y * TY;
+  const int zb0 = blockIdx.z * zblock;
+  const int zb1 = min(zb0 + zblock, L.nz);
+  const long long N = L.N;
+  const long long plane_sz = (long long)L.nx * L.ny;
+  const cx<R>* X = a.x + rhs * N;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = (gx < L.nx) && (gy < L.ny);
+  const R inv_ell2 = L.inv_ell2;
+  const cx<R> shift = a.mass_shift;
+  const cx<R> cshift = conjc(shift);
+  const int nseg = a.tab.nseg;
+  const R ds = a.tab.ds, inv_ds = a.tab.inv_ds;
+
+  cx<R> abx[3], acx[3], aby[3], acy[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int ix = min(max(gx + d - 1, 0), L.nx - 1), iy = min(max(gy + d - 1, 0), L.ny - 1);
+    abx[d] = L.abar[0][ix];
+    acx[d] = L.achk[0][ix];
+    aby[d] = L.abar[1][iy];
+    acy[d] = L.achk[1][iy];
+  }
+
+  auto load = [&](int z, int slot) {
+    cx<R> abz = (z >= 0 && z < L.nz) ? L.abar[2][z] : mkc<R>(1, 0);
+    for (int i = tid; i < PLANE; i += NT) {
+      int ly = i / PW, lx = i - ly * PW;
+      int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
+      bool in = (z >= 0) && (z < L.nz) && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
+      cx<R> v = mkc<R>(0, 0);
+      R prm[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) prm[j] = 0;
+      if (in) {
+        long long off = (long long)z * plane_sz + (long long)qy * L.nx + qx;
+        v = X[off];
+        R kap = L.kappa[off];
+        if (OP == OP_Q) {
+          R b[3];
+          table_eval<R, 5, 3>(sTab, nseg, ds, inv_ds, eta_star(kap), b);
+          prm[0] = b[0];
+          prm[1] = b[1] * (R)(1.0 / 6.0);
+          prm[2] = b[2] * (R)(1.0 / 12.0);
+          prm[3] = ((R)1 - b[0] - b[1] - b[2]) * (R)0.125;
+        } else {
+          R av[5];
+          table_eval<R, 0, 5>(sTab, nseg, ds, inv_ds, eta_star(kap), av);
+          prm[0] = av[3];
+          prm[1] = av[4] * (R)0.25;
+          prm[2] = ((R)1 - av[3] - av[4]) * (R)0.25;
+          prm[3] = av[0];
+          prm[4] = av[1] * (R)(1.0 / 6.0);
+          prm[5] = av[2] * (R)(1.0 / 12.0);
+          prm[6] = ((R)1 - av[0] - av[1] - av[2]) * (R)0.125;
+          prm[7] = inv_ell2 * kap * kap;
+          if (MODE == M_J2) {
+            cx<R> sab = L.abar[0][qx] + L.abar[1][qy] + abz;
+            cx<R> D = inv_ell2 * ((R)2 * prm[0] * sab) - (prm[7] * prm[3]) * shift;
+            v = a.omega_j * cdiv(v, conjc(D));   // y1 = omega D^-H g
+          }
+        }
+      }
+      sV[slot * PLANE + i] = v;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) sP[(slot * PLANE + i) * NP + j] = prm[j];
+    }
+  };
+
+  double nrm2 = 0.0;
+  load(zb0 - 1, (zb0 + 2) % 3);
+  load(zb0, zb0 % 3);
+  for (int z = zb0; z < zb1; ++z) {
+    load(z + 1, (z + 1) % 3);
+    __syncthreads();
+    if (active) {
+      cx<R> abz[3], acz[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int iz = min(max(z + d - 1, 0), L.nz - 1);
+        abz[d] = L.abar[2][iz];
+        acz[d] = L.achk[2][iz];
+      }
+      cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int slot = (z + dz + 3) % 3;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int li = slot * PLANE + (ty + 1 + dy) * PW + (tx + 1 + dx);
+            const cx<R> v = sV[li];
+            const R* p = sP + li * NP;
+            const int sh = (dx != 0) + (dy != 0) + (dz != 0);
+            if (OP == OP_Q) {
+              acc += p[sh] * v;
+            } else {
+              // row j = i + delta reaches i at offset -delta
+              auto dval = [&](cx<R> ab, cx<R> ac, int off) -> cx<R> {
+                return off == 0 ? (R)(-2) * ab : (off > 0 ? ab + ac : ab - ac);
+              };
+              cx<R> st = p[(dy != 0) + (dz != 0)] * dval(abx[dx + 1], acx[dx + 1], -dx) +
+                         p[(dx != 0) + (dz != 0)] * dval(aby[dy + 1], acy[dy + 1], -dy) +
+                         p[(dx != 0) + (dy != 0)] * dval(abz[dz + 1], acz[dz + 1], -dz);
+              cx<R> coef = (-inv_ell2) * conjc(st) - (p[7] * p[3 + sh]) * cshift;
+              acc += coef * v;
+            }
+          }
+        }
+      }
+      const long long idx = (long long)z * plane_sz + (long long)gy * L.nx + gx;
+      cx<R> out;
+      if (MODE == M_APPLY) {
+        out = acc;
+      } else if (MODE == M_RESID) {
+        out = a.g[rhs * N + idx] - acc;
+        nrm2 += (double)abs2(out);
+      } else {
+        const int li = (z % 3) * PLANE + (ty + 1) * PW + (tx + 1);
+        const R* p = sP + li * NP;
+        cx<R> sab = abx[1] + aby[1] + abz[1];
+        cx<R> Dh = conjc(inv_ell2 * ((R)2 * p[0] * sab) - (p[7] * p[3]) * shift);
+        if (MODE == M_J2) {
+          cx<R> g = X[idx];
+          out = sV[li] + a.omega_j * cdiv(g - acc, Dh);
+          if (a.base) out += a.base[rhs * N + idx];
+        } else {  // JSWEEP
+          out = sV[li] + a.omega_j * cdiv(a.g[rhs * N + idx] - acc, Dh);
+        }
+      }
+      a.y[rhs * N + idx] = out;
+    }
+    __syncthreads();
+  }
+  if (MODE == M_RESID && a.red.out) {
+    double s = block_sum(nrm2, sRed, tid, NT);
+    const unsigned nblk = (unsigned)(tiles_x * gridDim.y * gridDim.z);
+    const unsigned bid = (unsigned)(tile_x + tiles_x * (blockIdx.y + gridDim.y * blockIdx.z));
+    if (tid == 0) a.red.partial[(size_t)rhs * nblk + bid] = s;
+    if (last_block_arrive(a.red.count + rhs, nblk, tid)) {
+      double t = 0.0;
+      for (unsigned b = tid; b < nblk; b += NT) t += __ldcg(a.red.partial + (size_t)rhs * nblk + b);
+      t = block_sum(t, sRed, tid, NT);
+      if (tid == 0) {
+        a.red.out[rhs] = t;
+        if (a.red.root) a.red.root[rhs] = sqrt(t);
+        if (a.red.inv_root) a.red.inv_root[rhs] = t > 1e-300 ? 1.0 / sqrt(t) : 0.0;
+        a.red.count[rhs] = 0;
+      }
+    }
+  }
+}
+
+// One Jacobi sweep from zero: y = omega D^-1 g (pointwise; forward or adjoint).
+template <class R>
+__global__ void k_j1(StencilCall<R> a, int adjoint) {
+  const LevelView<R>& L = a.lv;
+  const long long n = L.N * a.nrhs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    long long i = t % L.N;
+    int x = (int)(i % L.nx);
+    int y = (int)((i / L.nx) % L.ny);
+    int z = (int)(i / ((long long)L.nx * L.ny));
+    R kap = L.kappa[i];
+    R av[5];
+    table_eval<R, 0, 5>(a.tab.coef, a.tab.nseg, a.tab.ds, a.tab.inv_ds, eta_star(kap), av);
+    cx<R> sab = L.abar[0][x] + L.abar[1][y] + L.abar[2][z];
+    cx<R> D = L.inv_ell2 * ((R)2 * av[3] * sab) - (L.inv_ell2 * kap * kap * av[0]) * a.mass_shift;
+    if (adjoint) D = conjc(D);
+    cx<R> out = a.omega_j * cdiv(a.x[t], D);
+    if (a.base) out += a.base[t];
+    a.y[t] = out;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launcher
+// ----------------------------------------------------------------------------
+static int choose_zblock(int nx, int ny, int nz, int nrhs) {
+  long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nrhs;
+  // aim for about 4 waves of 2 CTAs on 152 SMs, with at least 4 planes per CTA
+  long long want = 152LL * 2 * 4;
+  long long nzb = (want + tiles - 1) / tiles;
+  int zb = (int)((nz + nzb - 1) / nzb);
+  if (zb < 4) zb = 4;
+  if (zb > 64) zb = 64;
+  return zb;
+}
+
+template <class R, int MODE, int OP>
+static void launch_fwd_t(const StencilCall<R>& c, cudaStream_t s) {
+  const LevelView<R>& L = c.lv;
+  int zb = choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
+  int tiles_x = (L.nx + TX - 1) / TX;
+  dim3 grid(tiles_x * c.nrhs, (L.ny + TY - 1) / TY, (L.nz + zb - 1) / zb);
+  k_fwd<R, MODE, OP><<<grid, dim3(TX, TY), 0, s>>>(c, zb, tiles_x);
+}
+
+template <class R, int MODE, int OP>
+static void launch_adj_t(const StencilCall<R>& c, cudaStream_t s) {
+  constexpr int NP = AdjNP<OP>::v;
+  const LevelView<R>& L = c.lv;
+  int zb = choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
+  int tiles_x = (L.nx + TX - 1) / TX;
+  dim3 grid(tiles_x * c.nrhs, (L.ny + TY - 1) / TY, (L.nz + zb - 1) / zb);
+  size_t smem = 3 * PLANE * (sizeof(cx<R>) + NP * sizeof(R)) + kMaxSeg * kNumFn * 4 * sizeof(R);
+  k_adj<R, MODE, OP><<<grid, dim3(TX, TY), smem, s>>>(c, zb, tiles_x);
+}
+
+template <class R>
+void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s) {
+  if (mode == M_J1) {
+    long long n = c.lv.N * c.nrhs;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_j1<R><<<blocks, 256, 0, s>>>(c, adjoint ? 1 : 0);
+    return;
+  }
+  if (!adjoint) {
+    if (op == OP_Q) {
+      launch_fwd_t<R, M_APPLY, OP_Q>(c, s);
+      return;
+    }
+    switch (mode) {
+      case M_APPLY: launch_fwd_t<R, M_APPLY, OP_AB>(c, s); break;
+      case M_RESID: launch_fwd_t<R, M_RESID, OP_AB>(c, s); break;
+      case M_J2: launch_fwd_t<R, M_J2, OP_AB>(c, s); break;
+      case M_JSWEEP: launch_fwd_t<R, M_JSWEEP, OP_AB>(c, s); break;
+    }
+  } else {
+    if (op == OP_Q) {
+      launch_adj_t<R, M_APPLY, OP_Q>(c, s);
+      return;
+    }
+    switch (mode) {
+      case M_APPLY: launch_adj_t<R, M_APPLY, OP_AB>(c, s); break;
+      case M_RESID: launch_adj_t<R, M_RESID, OP_AB>(c, s); break;
+      case M_J2: launch_adj_t<R, M_J2, OP_AB>(c, s); break;
+      case M_JSWEEP: launch_adj_t<R, M_JSWEEP, OP_AB>(c, s); break;
+    }
+  }
+}
+
+template <class R, int MODE, int OP>
+static void set_adj_attr() {
+  constexpr int NP = AdjNP<OP>::v;
+  size_t smem = 3 * PLANE * (sizeof(cx<R>) + NP * sizeof(R)) + kMaxSeg * kNumFn * 4 * sizeof(R);
+  cudaFuncSetAttribute(k_adj<R, MODE, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Opt the adjoint kernels into more than 48 KB of dynamic shared memory (the
+// double-precision instances need about 82 KB).  Called before any launch and
+// outside stream capture.
+void init_kernel_attributes() {
+  set_adj_attr<float, M_APPLY, OP_AB>();
+  set_adj_attr<float, M_RESID, OP_AB>();
+  set_adj_attr<float, M_J2, OP_AB>();
+  set_adj_attr<float, M_JSWEEP, OP_AB>();
+  set_adj_attr<float, M_APPLY, OP_Q>();
+  set_adj_attr<double, M_APPLY, OP_AB>();
+  set_adj_attr<double, M_RESID, OP_AB>();
+  set_adj_attr<double, M_J2, OP_AB>();
+  set_adj_attr<double, M_JSWEEP, OP_AB>();
+  set_adj_attr<double, M_APPLY, OP_Q>();
+}
+
+template void launch_stencil<float>(const StencilCall<float>&, int, int, bool, cudaStream_t);
+template void launch_stencil<double>(const StencilCall<double>&, int, int, bool, cudaStream_t);
+
+}  // namespace hz

@@ -1,0 +1,755 @@
+// Grid transfers, Krylov vector passes, small dense solves and set-up kernels.
+//
+// Reductions are deterministic: each block reduces its elements in a fixed
+// tree (per-thread partial sums in the working precision, block and grid
+// combination in double), writes per-block partials, and the last block to
+// arrive (atomic arrival counter, no waiting) combines them in block order
+// and runs a small epilogue on the result.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "hz_kernels.h"
+
+namespace hz {
+
+constexpr int VB = 256;          // threads per block of vector kernels
+constexpr int KMAX = 16;         // largest Krylov basis handled by one pass
+
+static int vec_blocks(long long n) {
+  long long b = (n + VB * 4 - 1) / (VB * 4);
+  return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 8));
+}
+
+// ----------------------------------------------------------------------------
+// transfers
+// ----------------------------------------------------------------------------
+template <class R>
+__global__ void k_restrict(const cx<R>* __restrict__ f, cx<R>* __restrict__ c, int nxf, int nyf, int nzf, int nrhs) {
+  const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
+  const long long Nc = (long long)nxc * nyc * nzc, Nf = (long long)nxf * nyf * nzf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nc * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / Nc, i = t - r * Nc;
+    const int X = (int)(i % nxc), Y = (int)((i / nxc) % nyc), Z = (int)(i / ((long long)nxc * nyc));
+    const cx<R>* F = f + r * Nf;
+    cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int z = 2 * Z + dz;
+      if (z < 0 || z >= nzf) continue;
+      const R wz = dz == 0 ? (R)0.5 : (R)0.25;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = 2 * Y + dy;
+        if (y < 0 || y >= nyf) continue;
+        const R wzy = wz * (dy == 0 ? (R)0.5 : (R)0.25);
+        const cx<R>* row = F + ((long long)z * nyf + y) * nxf;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = 2 * X + dx;
+          if (x < 0 || x >= nxf) continue;
+          acc += (wzy * (dx == 0 ? (R)0.5 : (R)0.25)) * row[x];
+        }
+      }
+    }
+    c[t] = acc;
+  }
+}
+
+template <class R>
+__global__ void k_prolong_add(const cx<R>* __restrict__ c, const cx<R>* __restrict__ base, cx<R>* __restrict__ f,
+                              int nxf, int nyf, int nzf, int nrhs) {
+  const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
+  const long long Nc = (long long)nxc * nyc * nzc, Nf = (long long)nxf * nyf * nzf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nf * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / Nf, i = t - r * Nf;
+    const int x = (int)(i % nxf), y = (int)((i / nxf) % nyf), z = (int)(i / ((long long)nxf * nyf));
+    const cx<R>* C = c + r * Nc;
+    const int X0 = x >> 1, Y0 = y >> 1, Z0 = z >> 1;
+    const int ox = x & 1, oy = y & 1, oz = z & 1;
+    cx<R> acc = mkc<R>(0, 0);
+    for (int kz = 0; kz <= oz; ++kz)
+      for (int ky = 0; ky <= oy; ++ky)
+        for (int kx = 0; kx <= ox; ++kx) {
+          const R w = (ox ? (R)0.5 : (R)1) * (oy ? (R)0.5 : (R)1) * (oz ? (R)0.5 : (R)1);
+          acc += w * C[((long long)(Z0 + kz) * nyc + (Y0 + ky)) * nxc + (X0 + kx)];
+        }
+    f[t] = base ? base[t] + acc : acc;
+  }
+}
+
+template <class R>
+void launch_restrict(const cx<R>* fine, cx<R>* coarse, int nxf, int nyf, int nzf, int nrhs, cudaStream_t s) {
+  long long nc = (long long)((nxf - 1) / 2 + 1) * ((nyf - 1) / 2 + 1) * ((nzf - 1) / 2 + 1) * nrhs;
+  k_restrict<R><<<vec_blocks(nc), VB, 0, s>>>(fine, coarse, nxf, nyf, nzf, nrhs);
+}
+template <class R>
+void launch_prolong_add(const cx<R>* coarse, const cx<R>* base, cx<R>* fine, int nxf, int nyf, int nzf, int nrhs,
+                        cudaStream_t s) {
+  long long nf = (long long)nxf * nyf * nzf * nrhs;
+  k_prolong_add<R><<<vec_blocks(nf), VB, 0, s>>>(coarse, base, fine, nxf, nyf, nzf, nrhs);
+}
+
+// ----------------------------------------------------------------------------
+// multi-value block reduction: nv doubles per thread -> out[0..nv) in thread v
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum_multi(double* vals, int nv, double* sm /* [8][nv] */, int tid) {
+  const int lane = tid & 31, w = tid >> 5;
+  for (int v = 0; v < nv; ++v) {
+    double x = warp_sum(vals[v]);
+    if (lane == 0) sm[w * nv + v] = x;
+  }
+  __syncthreads();
+  if (tid < nv) {
+    double t = 0.0;
+    for (int k = 0; k < VB / 32; ++k) t += sm[k * nv + tid];
+    vals[0] = t;  // thread v holds value v
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// classical Gram-Schmidt passes
+// ----------------------------------------------------------------------------
+struct CgsArgs {
+  int n, nrhs, kn, ld;
+  long long vstride;
+  const double* coef;   // [rhs][ld] complex
+  bool update, dots, norm;
+  double* dots_out;     // [rhs][ld] complex
+  double* nrm_out;      // [rhs]
+  int epi;
+  double* H;            // per rhs: column-major (ldh x m) complex, ldh = ld
+  int col;
+  int hcols;            // m (columns per rhs)
+  double* scale_out;    // [rhs]
+  double* beta_out;     // [rhs]
+  Reduce red;
+};
+
+template <class R, int KN>
+__global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* __restrict__ w, CgsArgs a) {
+  constexpr int NVMAX = 2 * KMAX + 1;
+  __shared__ double sm[(VB / 32) * NVMAX];
+  __shared__ double sres[NVMAX];
+  __shared__ R scoef[2 * KMAX];
+  const int tid = threadIdx.x;
+  const int rhs = blockIdx.y;
+  const int kn = KN;
+  const long long N = a.n;
+  if (a.update && tid < kn) {
+    scoef[2 * tid] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid];
+    scoef[2 * tid + 1] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid + 1];
+  }
+  __syncthreads();
+  R acc[2 * KN + 1];
+#pragma unroll
+  for (int v = 0; v < 2 * KN + 1; ++v) acc[v] = 0;
+  cx<R>* W = w + rhs * N;
+  const cx<R>* Vr = V + rhs * N;
+  for (long long i = blockIdx.x * (long long)VB + tid; i < N; i += (long long)gridDim.x * VB) {
+    cx<R> wi = W[i];
+    if (a.update) {
+#pragma unroll
+      for (int k = 0; k < KN; ++k) wi -= mkc<R>(scoef[2 * k], scoef[2 * k + 1]) * Vr[k * a.vstride + i];
+      W[i] = wi;
+    }
+    if (a.dots) {
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        cx<R> p = cjmul(Vr[k * a.vstride + i], wi);
+        acc[2 * k] += p.x;
+        acc[2 * k + 1] += p.y;
+      }
+    }
+    if (a.norm) acc[2 * KN] += abs2(wi);
+  }
+  const int nv = 2 * KN + 1;
+  double vals[2 * KN + 1];
+#pragma unroll
+  for (int v = 0; v < 2 * KN + 1; ++v) vals[v] = (double)acc[v];
+  block_sum_multi(vals, nv, sm, tid);
+  const unsigned nblk = gridDim.x;
+  if (tid < nv) a.red.partial[((size_t)rhs * nblk + blockIdx.x) * nv + tid] = vals[0];
+  if (!last_block_arrive(a.red.count + rhs, nblk, tid)) return;
+  if (tid < nv) {
+    double t = 0.0;
+    for (unsigned b = 0; b < nblk; ++b) t += __ldcg(a.red.partial + ((size_t)rhs * nblk + b) * nv + tid);
+    sres[tid] = t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    a.red.count[rhs] = 0;
+    double* Hc = a.H ? a.H + ((size_t)rhs * a.hcols + (a.col >= 0 ? a.col : 0)) * a.ld * 2 : nullptr;
+    switch (a.epi) {
+      case EPI_STORE:
+        if (a.dots_out)
+          for (int k = 0; k < kn; ++k) {
+            a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
+            a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+          }
+        if (a.nrm_out) a.nrm_out[rhs] = sres[2 * KN];
+        break;
+      case EPI_ARNOLDI_FIRST:
+        for (int k = 0; k < kn; ++k) {
+          Hc[2 * k] = sres[2 * k];
+          Hc[2 * k + 1] = sres[2 * k + 1];
+          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
+          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+        }
+        break;
+      case EPI_ARNOLDI_SECOND:
+        for (int k = 0; k < kn; ++k) {
+          Hc[2 * k] += sres[2 * k];
+          Hc[2 * k + 1] += sres[2 * k + 1];
+          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
+          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+        }
+        break;
+      case EPI_NORMALISE: {
+        double nrm = sqrt(sres[2 * KN]);
+        if (a.col >= 0) {
+          Hc[2 * kn] = nrm;
+          Hc[2 * kn + 1] = 0.0;
+        }
+        if (a.beta_out) a.beta_out[rhs] = nrm;
+        // an exactly zero (or denormal) norm ends the Krylov space: the next
+        // basis vector is set to zero and the small solve ignores it
+        if (a.scale_out) a.scale_out[rhs] = (nrm > 1e-300) ? 1.0 / nrm : 0.0;
+        break;
+      }
+    }
+  }
+}
+
+template <class R, int KN>
+static void cgs_kn(const KrylovCall& k, const cx<R>* V, cx<R>* w, const CgsArgs& a, cudaStream_t s) {
+  dim3 grid(vec_blocks(k.n), k.nrhs);
+  k_cgs<R, KN><<<grid, VB, 0, s>>>(V, w, a);
+}
+
+template <class R>
+void launch_cgs(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coef, bool update, bool dots,
+                bool norm, double* dots_out, double* nrm_out, int epi, double* H, int col, double* scale_out,
+                double* beta_out, const Reduce& red, cudaStream_t s) {
+  CgsArgs a;
+  a.n = k.n;
+  a.nrhs = k.nrhs;
+  a.kn = k.kn;
+  a.ld = k.ld;
+  a.vstride = k.vstride;
+  a.coef = coef;
+  a.update = update;
+  a.dots = dots;
+  a.norm = norm;
+  a.dots_out = dots_out;
+  a.nrm_out = nrm_out;
+  a.epi = epi;
+  a.H = H;
+  a.col = col;
+  a.hcols = k.ld - 1;
+  a.scale_out = scale_out;
+  a.beta_out = beta_out;
+  a.red = red;
+  switch (k.kn) {
+#define HZ_KN(K) \
+  case K: cgs_kn<R, K>(k, V, w, a, s); break;
+    HZ_KN(0) HZ_KN(1) HZ_KN(2) HZ_KN(3) HZ_KN(4) HZ_KN(5) HZ_KN(6) HZ_KN(7) HZ_KN(8) HZ_KN(9) HZ_KN(10) HZ_KN(11)
+    HZ_KN(12) HZ_KN(13) HZ_KN(14) HZ_KN(15) HZ_KN(16)
+#undef HZ_KN
+    default: break;
+  }
+}
+
+template <class R>
+void launch_norm2(const cx<R>* v, int n, int nrhs, const Reduce& red, cudaStream_t s) {
+  KrylovCall k;
+  k.n = n;
+  k.nrhs = nrhs;
+  k.kn = 0;
+  k.ld = 1;
+  launch_cgs<R>(k, v, const_cast<cx<R>*>(v), nullptr, false, false, true, nullptr, red.out, EPI_STORE, nullptr, -1,
+                nullptr, nullptr, red, s);
+}
+
+// ----------------------------------------------------------------------------
+// scale / combine / axpy / copy
+// ----------------------------------------------------------------------------
+template <class R>
+__global__ void k_scale(const cx<R>* __restrict__ w, cx<R>* __restrict__ out, const double* __restrict__ scale, int n,
+                        int nrhs) {
+  const int rhs = blockIdx.y;
+  const R sc = (R)scale[rhs];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[(long long)rhs * n + i] = sc * w[(long long)rhs * n + i];
+}
+template <class R>
+void launch_scale(const cx<R>* w, cx<R>* out, const double* scale, int n, int nrhs, cudaStream_t s) {
+  k_scale<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(w, out, scale, n, nrhs);
+}
+
+template <class R>
+__global__ void k_combine(const cx<R>* __restrict__ Z, long long zstride, int kn, const double* __restrict__ y, int ld,
+                          const cx<R>* __restrict__ x0, cx<R>* __restrict__ x, int n) {
+  __shared__ R sy[2 * KMAX];
+  const int rhs = blockIdx.y;
+  if (threadIdx.x < 2 * kn) sy[threadIdx.x] = (R)y[(size_t)rhs * ld * 2 + threadIdx.x];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)rhs * n + i;
+    cx<R> acc = x0 ? x0[o] : mkc<R>(0, 0);
+    for (int k = 0; k < kn; ++k) acc += mkc<R>(sy[2 * k], sy[2 * k + 1]) * Z[k * zstride + o];
+    x[o] = acc;
+  }
+}
+template <class R>
+void launch_combine(const cx<R>* Z, long long zstride, int kn, const double* y, int ld, const cx<R>* x0, cx<R>* x,
+                    int n, int nrhs, cudaStream_t s) {
+  k_combine<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(Z, zstride, kn, y, ld, x0, x, n);
+}
+
+template <class R>
+__global__ void k_axpy(const cx<R>* __restrict__ x, cx<R>* __restrict__ y, R ar, R ai, long long n) {
+  const cx<R> a = mkc<R>(ar, ai);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+template <class R>
+void launch_axpy(const cx<R>* x, cx<R>* y, double ar, double ai, long long n, cudaStream_t s) {
+  k_axpy<R><<<vec_blocks(n), VB, 0, s>>>(x, y, (R)ar, (R)ai, n);
+}
+template <class R>
+__global__ void k_copy(const cx<R>* __restrict__ x, cx<R>* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+template <class R>
+void launch_copy(const cx<R>* x, cx<R>* y, long long n, cudaStream_t s) {
+  k_copy<R><<<vec_blocks(n), VB, 0, s>>>(x, y, n);
+}
+template <class R>
+__global__ void k_zero(cx<R>* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mkc<R>(0, 0);
+}
+template <class R>
+void launch_zero(cx<R>* y, long long n, cudaStream_t s) {
+  k_zero<R><<<vec_blocks(n), VB, 0, s>>>(y, n);
+}
+
+__global__ void k_c128_to_c64(const cx<double>* __restrict__ in, cx<float>* __restrict__ out,
+                              const double* __restrict__ scale, int n) {
+  const int rhs = blockIdx.y;
+  const double sc = scale[rhs];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    cx<double> v = in[(long long)rhs * n + i];
+    out[(long long)rhs * n + i] = mkc<float>((float)(v.x * sc), (float)(v.y * sc));
+  }
+}
+void launch_c128_to_c64_scaled(const cx<double>* in, cx<float>* out, const double* scale, int n, int nrhs,
+                               cudaStream_t s) {
+  k_c128_to_c64<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(in, out, scale, n);
+}
+__global__ void k_add_c64_to_c128(const cx<float>* __restrict__ d, cx<double>* __restrict__ x,
+                                  const double* __restrict__ scale, int n) {
+  const int rhs = blockIdx.y;
+  const double sc = scale[rhs];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    cx<float> v = d[(long long)rhs * n + i];
+    cx<double>& t = x[(long long)rhs * n + i];
+    t.x += sc * (double)v.x;
+    t.y += sc * (double)v.y;
+  }
+}
+void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const double* scale, int n, int nrhs,
+                                   cudaStream_t s) {
+  k_add_c64_to_c128<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(d, x, scale, n);
+}
+
+// ----------------------------------------------------------------------------
+// small least squares by complex Givens rotations (one thread per rhs)
+// ----------------------------------------------------------------------------
+struct Cd {
+  double x, y;
+};
+__device__ __forceinline__ Cd cd(double a, double b) { return Cd{a, b}; }
+__device__ __forceinline__ Cd cmulD(Cd a, Cd b) { return cd(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ Cd caddD(Cd a, Cd b) { return cd(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ Cd csubD(Cd a, Cd b) { return cd(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ Cd cconjD(Cd a) { return cd(a.x, -a.y); }
+__device__ __forceinline__ double cabsD(Cd a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ Cd cdivD(Cd a, Cd b) {
+  double d = b.x * b.x + b.y * b.y;
+  return cd((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Solve min || beta e_1 - H y || for H (m+1) x m upper Hessenberg (column-major,
+// leading dim ldh, entries (re, im)); y (m entries) written to yout.
+__device__ void givens_lsq(const double* H, int ldh, int m, double beta, double* yout) {
+  Cd R[KMAX + 1][KMAX];
+  Cd g[KMAX + 1];
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) R[i][j] = cd(H[(j * ldh + i) * 2], H[(j * ldh + i) * 2 + 1]);
+  for (int i = 0; i <= m; ++i) g[i] = cd(0, 0);
+  g[0] = cd(beta, 0);
+  for (int j = 0; j < m; ++j) {
+    Cd a = R[j][j], b = R[j + 1][j];
+    double na = cabsD(a), nb = cabsD(b);
+    double r = hypot(na, nb);
+    double c;
+    Cd s;
+    if (r == 0.0) {
+      c = 1.0;
+      s = cd(0, 0);
+    } else if (na == 0.0) {
+      c = 0.0;
+      s = cd(1, 0);
+    } else {
+      c = na / r;
+      Cd ua = cd(a.x / na, a.y / na);
+      s = cmulD(ua, cd(b.x / r, -b.y / r));
+    }
+    for (int k = j; k < m; ++k) {
+      Cd t1 = R[j][k], t2 = R[j + 1][k];
+      R[j][k] = caddD(cd(c * t1.x, c * t1.y), cmulD(s, t2));
+      R[j + 1][k] = csubD(cd(c * t2.x, c * t2.y), cmulD(cconjD(s), t1));
+    }
+    Cd g1 = g[j], g2 = g[j + 1];
+    g[j] = caddD(cd(c * g1.x, c * g1.y), cmulD(s, g2));
+    g[j + 1] = csubD(cd(c * g2.x, c * g2.y), cmulD(cconjD(s), g1));
+  }
+  Cd y[KMAX];
+  for (int i = m - 1; i >= 0; --i) {
+    Cd t = g[i];
+    for (int k = i + 1; k < m; ++k) t = csubD(t, cmulD(R[i][k], y[k]));
+    y[i] = (cabsD(R[i][i]) > 0.0) ? cdivD(t, R[i][i]) : cd(0, 0);
+  }
+  for (int i = 0; i < m; ++i) {
+    yout[2 * i] = y[i].x;
+    yout[2 * i + 1] = y[i].y;
+  }
+}
+
+__global__ void k_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  givens_lsq(H + (size_t)r * m * (m + 1) * 2, m + 1, m, beta[r], y + (size_t)r * ld * 2);
+}
+void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s) {
+  k_lsq<<<(nrhs + 31) / 32, 32, 0, s>>>(H, beta, y, m, ld, nrhs);
+}
+
+// ----------------------------------------------------------------------------
+// CA-GMRES bottom solve: Gram matrix of [p_0 .. p_s], CholQR, least squares
+// ----------------------------------------------------------------------------
+template <class R, int KN>
+__global__ void __launch_bounds__(VB) k_gram(const cx<R>* __restrict__ P, long long pstride, int n, double* y, int ld,
+                                             Reduce red) {
+  constexpr int NG = KN * (KN + 1) / 2;
+  constexpr int NV = 2 * NG;
+  __shared__ double sm[(VB / 32) * NV];
+  __shared__ double sres[NV];
+  const int tid = threadIdx.x, rhs = blockIdx.y;
+  R acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0;
+  const cx<R>* Pr = P + (long long)rhs * n;
+  for (long long i = blockIdx.x * (long long)VB + tid; i < n; i += (long long)gridDim.x * VB) {
+    cx<R> p[KN];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) p[k] = Pr[k * pstride + i];
+    int q = 0;
+#pragma unroll
+    for (int a = 0; a < KN; ++a)
+#pragma unroll
+      for (int b = a; b < KN; ++b) {
+        cx<R> t = cjmul(p[a], p[b]);
+        acc[2 * q] += t.x;
+        acc[2 * q + 1] += t.y;
+        ++q;
+      }
+  }
+  double vals[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = (double)acc[v];
+  block_sum_multi(vals, NV, sm, tid);
+  const unsigned nblk = gridDim.x;
+  if (tid < NV) red.partial[((size_t)rhs * nblk + blockIdx.x) * NV + tid] = vals[0];
+  if (!last_block_arrive(red.count + rhs, nblk, tid)) return;
+  if (tid < NV) {
+    double t = 0.0;
+    for (unsigned b = 0; b < nblk; ++b) t += __ldcg(red.partial + ((size_t)rhs * nblk + b) * NV + tid);
+    sres[tid] = t;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  red.count[rhs] = 0;
+  // Hermitian Gram G[a][b] = <p_a, p_b>
+  Cd G[KN][KN];
+  int q = 0;
+  for (int a = 0; a < KN; ++a)
+    for (int b = a; b < KN; ++b) {
+      G[a][b] = cd(sres[2 * q], sres[2 * q + 1]);
+      G[b][a] = cconjD(G[a][b]);
+      ++q;
+    }
+  // Cholesky G = U^H U (U upper triangular); a pivot that is not clearly
+  // positive ends the basis there (the remaining directions are dropped).
+  Cd U[KN][KN];
+  for (int a = 0; a < KN; ++a)
+    for (int b = 0; b < KN; ++b) U[a][b] = cd(0, 0);
+  const double g00 = G[0][0].x;
+  int rank = KN;
+  for (int j = 0; j < KN; ++j) {
+    double d = G[j][j].x;
+    for (int k = 0; k < j; ++k) d -= U[k][j].x * U[k][j].x + U[k][j].y * U[k][j].y;
+    if (!(d > 1e-13 * g00) || !(g00 > 0.0)) {
+      rank = j;
+      break;
+    }
+    double ujj = sqrt(d);
+    U[j][j] = cd(ujj, 0);
+    for (int b = j + 1; b < KN; ++b) {
+      Cd t = G[j][b];
+      for (int k = 0; k < j; ++k) t = csubD(t, cmulD(cconjD(U[k][j]), U[k][b]));
+      U[j][b] = cd(t.x / ujj, t.y / ujj);
+    }
+  }
+  // min || U e_0 - U[:, 1:] y ||, U[:,1:] is upper Hessenberg with first column
+  // (U01, U11, 0 ...); rhs U e_0 = U00 e_0.
+  const int m = KN - 1;
+  double Hs[(KMAX + 1) * KMAX * 2];
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) {
+      Cd v = (j + 1 < rank && i <= j + 1) ? U[i][j + 1] : cd(0, 0);
+      Hs[(j * (m + 1) + i) * 2] = v.x;
+      Hs[(j * (m + 1) + i) * 2 + 1] = v.y;
+    }
+  double beta = rank > 0 ? U[0][0].x : 0.0;
+  givens_lsq(Hs, m + 1, m, beta, y + (size_t)rhs * ld * 2);
+}
+
+template <class R>
+void launch_gram_lsq(const cx<R>* P, long long pstride, int kn, int n, int nrhs, double* y, int ld,
+                     const Reduce& red, cudaStream_t s) {
+  dim3 grid(vec_blocks(n), nrhs);
+  switch (kn) {
+    case 2: k_gram<R, 2><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 3: k_gram<R, 3><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 4: k_gram<R, 4><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 5: k_gram<R, 5><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 6: k_gram<R, 6><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 7: k_gram<R, 7><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    default: break;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// set-up, sources, receivers
+// ----------------------------------------------------------------------------
+template <class R>
+__global__ void k_setup_kappa(const double* __restrict__ c, int nxf, int nyf, int nzf, int n_pml, int stride,
+                              double omega, double ell, R* __restrict__ kappa) {
+  const int nx = (nxf - 1) / stride + 1, ny = (nyf - 1) / stride + 1, nz = (nzf - 1) / stride + 1;
+  const long long N = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    int X = (int)(i % nx), Y = (int)((i / nx) % ny), Z = (int)(i / ((long long)nx * ny));
+    int fx = min(max(X * stride, n_pml), nxf - 1 - n_pml);
+    int fy = min(max(Y * stride, n_pml), nyf - 1 - n_pml);
+    int fz = min(max(Z * stride, n_pml), nzf - 1 - n_pml);
+    double cv = c[((long long)fz * nyf + fy) * nxf + fx];
+    kappa[i] = (R)(omega * ell / cv);
+  }
+}
+template <class R>
+void launch_setup_kappa(const double* c, int nxf, int nyf, int nzf, int n_pml, int stride, double omega,
+                        double ell, R* kappa, cudaStream_t s) {
+  long long n = (long long)((nxf - 1) / stride + 1) * ((nyf - 1) / stride + 1) * ((nzf - 1) / stride + 1);
+  k_setup_kappa<R><<<vec_blocks(n), VB, 0, s>>>(c, nxf, nyf, nzf, n_pml, stride, omega, ell, kappa);
+}
+
+template <class R>
+__global__ void k_point_sources(const int* idx3, const double* amp, int nsrc, int nx, int ny, int nz, double scale,
+                                cx<R>* f) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsrc) return;
+  long long N = (long long)nx * ny * nz;
+  int ix = idx3[3 * s], iy = idx3[3 * s + 1], iz = idx3[3 * s + 2];
+  long long i = ((long long)iz * ny + iy) * nx + ix;
+  f[(long long)s * N + i] = mkc<R>((R)(amp[2 * s] * scale), (R)(amp[2 * s + 1] * scale));
+}
+template <class R>
+void launch_point_sources(const int* idx3, const double* amp, int nsrc, int nx, int ny, int nz, double scale,
+                          cx<R>* f, cudaStream_t s) {
+  k_point_sources<R><<<(nsrc + 63) / 64, 64, 0, s>>>(idx3, amp, nsrc, nx, ny, nz, scale, f);
+}
+
+template <class R>
+__global__ void k_gather(const cx<R>* u, const int* rec, int nrec, int n, int nrhs, cx<double>* out) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nrec * nrhs) return;
+  int r = (int)(t / nrec), q = (int)(t % nrec);
+  out[t] = cvt<double>(u[(long long)r * n + rec[q]]);
+}
+template <class R>
+void launch_gather(const cx<R>* u, const int* rec, int nrec, int n, int nrhs, cx<double>* out, cudaStream_t s) {
+  long long t = (long long)nrec * nrhs;
+  k_gather<R><<<(int)((t + 255) / 256), 256, 0, s>>>(u, rec, nrec, n, nrhs, out);
+}
+// receivers are distinct nodes, so the scatter has no write conflicts
+template <class R>
+__global__ void k_scatter(const cx<double>* vals, const int* rec, int nrec, int n, int nrhs, cx<R>* out) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nrec * nrhs) return;
+  int r = (int)(t / nrec), q = (int)(t % nrec);
+  out[(long long)r * n + rec[q]] = cvt<R>(vals[t]);
+}
+template <class R>
+void launch_scatter(const cx<double>* vals, const int* rec, int nrec, int n, int nrhs, cx<R>* out, cudaStream_t s) {
+  long long t = (long long)nrec * nrhs;
+  k_scatter<R><<<(int)((t + 255) / 256), 256, 0, s>>>(vals, rec, nrec, n, nrhs, out);
+}
+
+// ----------------------------------------------------------------------------
+// explicit instantiations
+// ----------------------------------------------------------------------------
+#define HZ_INST(R)                                                                                                   \
+  template void launch_restrict<R>(const cx<R>*, cx<R>*, int, int, int, int, cudaStream_t);                        \
+  template void launch_prolong_add<R>(const cx<R>*, const cx<R>*, cx<R>*, int, int, int, int, cudaStream_t);       \
+  template void launch_cgs<R>(const KrylovCall&, const cx<R>*, cx<R>*, const double*, bool, bool, bool, double*,   \
+                              double*, int, double*, int, double*, double*, const Reduce&, cudaStream_t);          \
+  template void launch_norm2<R>(const cx<R>*, int, int, const Reduce&, cudaStream_t);                              \
+  template void launch_scale<R>(const cx<R>*, cx<R>*, const double*, int, int, cudaStream_t);                      \
+  template void launch_combine<R>(const cx<R>*, long long, int, const double*, int, const cx<R>*, cx<R>*, int, int, \
+                                  cudaStream_t);                                                                   \
+  template void launch_gram_lsq<R>(const cx<R>*, long long, int, int, int, double*, int, const Reduce&,             \
+                                   cudaStream_t);                                                                  \
+  template void launch_axpy<R>(const cx<R>*, cx<R>*, double, double, long long, cudaStream_t);                     \
+  template void launch_copy<R>(const cx<R>*, cx<R>*, long long, cudaStream_t);                                     \
+  template void launch_zero<R>(cx<R>*, long long, cudaStream_t);                                                   \
+  template void launch_setup_kappa<R>(const double*, int, int, int, int, int, double, double, R*, cudaStream_t);    \
+  template void launch_point_sources<R>(const int*, const double*, int, int, int, int, double, cx<R>*,              \
+                                        cudaStream_t);                                                             \
+  template void launch_gather<R>(const cx<R>*, const int*, int, int, int, cx<double>*, cudaStream_t);               \
+  template void launch_scatter<R>(const cx<double>*, const int*, int, int, int, cx<R>*, cudaStream_t);
+HZ_INST(float)
+HZ_INST(double)
+#undef HZ_INST
+
+}  // namespace hz
+
+// ----------------------------------------------------------------------------
+// adjoint-state gradient, PML fold, shell coefficients (double precision)
+// ----------------------------------------------------------------------------
+namespace hz {
+
+__global__ void k_gradient(LevelView<double> L, TableView<double> T, double omega_h, const cx<double>* __restrict__ v,
+                           const cx<double>* __restrict__ lam, const cx<double>* __restrict__ f,
+                           const cx<double>* __restrict__ rr, int nrhs, double* __restrict__ g) {
+  const long long N = L.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.nx), y = (int)((i / L.nx) % L.ny), z = (int)(i / ((long long)L.nx * L.ny));
+    const double kap = L.kappa[i];
+    const double eta_raw = kap * kInv2Pi;
+    const double eta = eta_raw < kEtaMax ? eta_raw : kEtaMax;
+    // d eta / d m with kappa^2 = (omega h)^2 m; zero where the clamp is active
+    const double deta = eta_raw < kEtaMax ? (omega_h * omega_h) / (4.0 * 3.14159265358979323846 * kap) : 0.0;
+    double av[5], dav[5], bv[3], dbv[3];
+    table_eval_d<double, 0, 5>(T.coef, T.nseg, T.ds, T.inv_ds, eta, av, dav);
+    table_eval_d<double, 5, 3>(T.coef, T.nseg, T.ds, T.inv_ds, eta, bv, dbv);
+    for (int j = 0; j < 5; ++j) dav[j] *= deta;
+    for (int j = 0; j < 3; ++j) dbv[j] *= deta;
+    const double dt[3] = {dav[3], dav[4] * 0.25, -(dav[3] + dav[4]) * 0.25};
+    const double w[4] = {av[0], av[1] / 6.0, av[2] / 12.0, (1.0 - av[0] - av[1] - av[2]) * 0.125};
+    const double dw[4] = {dav[0], dav[1] / 6.0, dav[2] / 12.0, -(dav[0] + dav[1] + dav[2]) * 0.125};
+    const double dq[4] = {dbv[0], dbv[1] / 6.0, dbv[2] / 12.0, -(dbv[0] + dbv[1] + dbv[2]) * 0.125};
+    const double dk2 = omega_h * omega_h;  // d kappa^2 / d m
+    const cx<double> ab[3] = {L.abar[0][x], L.abar[1][y], L.abar[2][z]};
+    const cx<double> ac[3] = {L.achk[0][x], L.achk[1][y], L.achk[2][z]};
+    double acc = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      cx<double> dAv = mkc(0.0, 0.0), dQv = mkc(0.0, 0.0), dQf = mkc(0.0, 0.0);
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int qz = z + dz;
+        if (qz < 0 || qz >= L.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int qy = y + dy;
+          if (qy < 0 || qy >= L.ny) continue;
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int qx = x + dx;
+            if (qx < 0 || qx >= L.nx) continue;
+            const long long j = (long long)r * N + ((long long)qz * L.ny + qy) * L.nx + qx;
+            const int d[3] = {dx, dy, dz};
+            cx<double> st = mkc(0.0, 0.0);
+            for (int a = 0; a < 3; ++a) {
+              const int cls = (d[(a + 1) % 3] != 0) + (d[(a + 2) % 3] != 0);
+              const cx<double> dd = d[a] == 0 ? -2.0 * ab[a] : (d[a] > 0 ? ab[a] + ac[a] : ab[a] - ac[a]);
+              st += dt[cls] * dd;
+            }
+            const int sh = (dx != 0) + (dy != 0) + (dz != 0);
+            const cx<double> dA = (-L.inv_ell2) * st - mkc(L.inv_ell2 * (dk2 * w[sh] + kap * kap * dw[sh]), 0.0);
+            const cx<double> vj = v[j];
+            dAv += dA * vj;
+            dQv += dq[sh] * vj;
+            dQf += dq[sh] * f[j];
+          }
+        }
+      }
+      const long long o = (long long)r * N + i;
+      const cx<double> t1 = cjmul(lam[o], dQf - dAv);
+      const cx<double> t2 = cjmul(rr[o], dQv);
+      acc += t1.x + t2.x;
+    }
+    g[i] += acc;
+  }
+}
+
+void launch_gradient(const LevelView<double>& lv, const TableView<double>& tab, double omega_h,
+                     const cx<double>* v, const cx<double>* lam, const cx<double>* f, const cx<double>* rres,
+                     int nrhs, double* g_ext, cudaStream_t s) {
+  k_gradient<<<vec_blocks(lv.N), VB, 0, s>>>(lv, tab, omega_h, v, lam, f, rres, nrhs, g_ext);
+}
+
+__global__ void k_fold_pml(const double* __restrict__ ge, double* __restrict__ g, int nx, int ny, int nz, int p) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+    const int lo = p, hx = nx - 1 - p, hy = ny - 1 - p, hz = nz - 1 - p;
+    if (x < lo || x > hx || y < lo || y > hy || z < lo || z > hz) {
+      g[i] = 0.0;
+      continue;
+    }
+    const int x0 = x == lo ? 0 : x, x1 = x == hx ? nx - 1 : x;
+    const int y0 = y == lo ? 0 : y, y1 = y == hy ? ny - 1 : y;
+    const int z0 = z == lo ? 0 : z, z1 = z == hz ? nz - 1 : z;
+    double acc = 0.0;
+    for (int c = z0; c <= z1; ++c)
+      for (int b = y0; b <= y1; ++b)
+        for (int a = x0; a <= x1; ++a) acc += ge[((long long)c * ny + b) * nx + a];
+    g[i] = acc;
+  }
+}
+void launch_fold_pml(const double* g_ext, double* g, int nx, int ny, int nz, int n_pml, cudaStream_t s) {
+  k_fold_pml<<<vec_blocks((long long)nx * ny * nz), VB, 0, s>>>(g_ext, g, nx, ny, nz, n_pml);
+}
+
+__global__ void k_shell_coeffs(LevelView<double> L, TableView<double> T, double* out) {
+  const long long N = L.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double kap = L.kappa[i];
+    double a[5];
+    table_eval<double, 0, 5>(T.coef, T.nseg, T.ds, T.inv_ds, eta_star(kap), a);
+    const double k2 = kap * kap;
+    out[i] = 6.0 * a[3] - k2 * a[0];
+    out[N + i] = -a[3] + a[4] - k2 * a[1] / 6.0;
+    out[2 * N + i] = -a[4] / 2.0 + (1.0 - a[3] - a[4]) / 2.0 - k2 * a[2] / 12.0;
+    out[3 * N + i] = -0.75 * (1.0 - a[3] - a[4]) - k2 * (1.0 - a[0] - a[1] - a[2]) / 8.0;
+  }
+}
+void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& tab, double* out, cudaStream_t s) {
+  k_shell_coeffs<<<vec_blocks(lv.N), VB, 0, s>>>(lv, tab, out);
+}
+
+}  // namespace hz
