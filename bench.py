@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: three-grid preconditioned FGMRES solve of the IOFD Helmholtz
+system on one GB300 (or N replicas), plus the stencil roofline.
+
+Workload (default): Gaussian lens, 256^3 interior + 16-point PML (288^3
+intervals, 289^3 = 24.1 M fine nodes), ppw 6 at the minimum velocity, one
+centre source, complex64 hierarchy with FP64 outer Krylov scalars and FP64
+iterative refinement to relative residual 1e-6.
+
+One step = one helmholtz_solve call (b = Q f, FGMRES + Algorithm 1 with FP64
+refinement, u = Q v) on the resident model.  The headline value is the
+fine-grid update rate N_h * nrhs * PC_calls / t_step (one update = one fine
+node through one outer FGMRES step with its three-grid preconditioner call),
+summed over ranks.  Replicas (N > 1) solve independent copies: no collective
+on the data path ("scaling": "weak").
+
+--impl reference times the CPU oracle (the plain complex128 implementation
+of the paper's method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fine-grid stencil GUpdates/s (%HBM peak); time-to-solution at rel res 1e-6 vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + CLOCK_Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, dev=None):
+    if pg is not None:
+        import torch
+        pg.barrier(device_ids=[dev] if dev is not None else None)
+
+
+def allreduce_max(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing: the reference arm and the cpu_baseline leg
+# ----------------------------------------------------------------------------
+ORACLE_SAMPLE_N = 48
+
+
+def oracle_sample(workload_name):
+    """Full oracle solve (FGMRES + Algorithm 1, complex128) of the same medium
+    recipe on a 48^3 grid (8-point PML, ppw 6) to 1e-6; returns the update
+    rate in GUpdates/s, seconds and a description."""
+    import numpy as np
+    import hz_workloads as W
+    from oracle import iofd
+    from oracle import threegrid as tg
+    if workload_name == "gaussian_lens":
+        w = W.gaussian_lens(n=ORACLE_SAMPLE_N, n_pml=8)
+    elif workload_name == "layered_inclusion":
+        w = W.layered_inclusion(n=ORACLE_SAMPLE_N, n_pml=8, nsrc=1)
+    else:
+        w = W.homogeneous(n=ORACLE_SAMPLE_N, n_pml=8)
+    t0 = time.perf_counter()
+    prob = iofd.make_problem(w.c, w.n_pml, w.h, w.omega, w.gamma_max)
+    Q = iofd.operator_Q(prob)
+    b = Q(iofd.point_sources(prob, w.sources[:1])[0])
+    v, info = tg.solve(prob, b, tg.Params(tol=1e-6))
+    dt = time.perf_counter() - t0
+    N = w.N
+    value = N * info.pc_calls / dt / 1e9
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+    cores = int(threads) if threads else (os.cpu_count() or 1)
+    desc = (f"oracle (numpy complex128) full solve to 1e-6 of the {w.name} recipe at {w.n}^3 "
+            f"({N} nodes, {info.pc_calls} PC calls, {dt:.1f} s); rate = N*PC/t")
+    return value, dt, cores, desc
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        v, dt, cores, desc = oracle_sample("gaussian_lens")
+        vals.append((v, dt))
+    t_all = time.perf_counter() - t_all
+    value = statistics.median([v for v, _ in vals])
+    ms = 1000.0 * statistics.median([d for _, d in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GUpdates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "gaussian_lens_288", "sample": f"gaussian_lens_{ORACLE_SAMPLE_N}"},
+            "cpu_baseline": {"value": value, "unit": "GUpdates/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "GUpdates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import hz_workloads as W
+    import paper_2608_22946_gb300 as hz
+
+    world, rank, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    w = {"2": W.gaussian_lens, "1": W.homogeneous, "3": W.layered_inclusion}[args.config]()
+    if args.config == "3":
+        sources = w.sources
+        nrhs = len(sources)
+    else:
+        sources = w.sources[:1]
+        nrhs = 1
+    params = hz.default_params(tol=1e-6, precision=hz.HZ_C64)
+    c_host = torch.from_numpy(w.c.reshape(-1)).pin_memory()
+    c_dev = c_host.to("cuda", non_blocking=True)
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, c_dev, params=params, max_nrhs=nrhs)
+    N = w.N
+    v = torch.empty((nrhs,) + s.shape, dtype=torch.complex128, device="cuda")
+    u = torch.empty_like(v)
+    for _ in range(args.warmup):
+        s.helmholtz_solve(sources, v_out=v, u_out=u)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    l0 = hz.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u)
+            stats.append(st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(pg, dev)
+    launches = hz.kernel_launches() - l0
+    t_step = ev0.elapsed_time(ev1) / 1000.0 / args.steps
+    t_step = allreduce_max(pg, t_step)
+    pc = stats[-1]["pc_calls"]
+    rel = max(st["rel_res"] for st in stats)
+    value = N * nrhs * pc * world / t_step / 1e9
+
+    result = {"metric": METRIC, "value": value, "unit": "GUpdates/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+              "data": "synthetic (seeded Gaussian-lens velocity, point source)",
+              "config": {"workload": {"2": "gaussian_lens_288", "1": "homogeneous_48",
+                                      "3": "layered_inclusion_224x16"}[args.config],
+                         "grid_intervals": w.n, "n_pml": w.n_pml, "fine_nodes": N, "nrhs": nrhs,
+                         "ppw": 6, "tol": 1e-6, "precision": "c64 hierarchy, FP64 outer scalars + refinement",
+                         "parallelism": f"replicas x{world}",
+                         "l2": "inputs larger than L2 (each fine complex64 vector 193 MB)"},
+              "time_to_solution_s": t_step, "pc_calls": pc, "rel_res": rel,
+              "refine_passes": stats[-1]["refine_passes"], "t_setup_s": stats[-1]["t_setup"],
+              "gpu_launches": int(launches), "clocks": clk.summary()}
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        # --- roofline of the dominant kernel: the fine-grid complex64 stencil
+        x = torch.randn((nrhs,) + s.shape, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+        K = 20
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_k = e0.elapsed_time(e1) / 1000.0 / K
+        bytes_per_node = 8 + 4 + 8  # read x (c64), kappa (fp32), write y (c64)
+        achieved = bytes_per_node * N * nrhs / t_k / 1e9
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+        if os.path.exists(tf):
+            with open(tf) as f:
+                traffic = json.load(f).get("bytes_per_launch_fine_288")
+        result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                              "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                              "kernel": "k_fwd<float,APPLY,AB> (A_h, complex64, fine grid)",
+                              "peak_kind": pk_kind, "gupdates_per_s": N * nrhs / t_k / 1e9,
+                              "avg_launch_ms": 1000 * t_k}
+        del x, y
+        # --- FP64 comparison: the plain complex128 GPU solve (outside the timed region)
+        if not args.no_fp64:
+            p64 = hz.default_params(tol=1e-6, precision=hz.HZ_C128)
+            s64 = hz.Solver(w.n, w.n_pml, w.h, w.omega, c_dev, params=p64, max_nrhs=1)
+            v64 = torch.empty((1,) + s.shape, dtype=torch.complex128, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, st64 = s64.helmholtz_solve(sources[:1], v_out=v64, want_u=False)
+            torch.cuda.synchronize()
+            t64 = time.perf_counter() - t0
+            err = float(torch.linalg.vector_norm(v[0] - v64[0]) / torch.linalg.vector_norm(v64[0]))
+            result["fp64_solve"] = {"time_to_solution_s": t64, "pc_calls": st64["pc_calls"],
+                                    "rel_res": st64["rel_res"], "mixed_vs_fp64_rel_l2": err,
+                                    "speedup_mixed_over_fp64": t64 / (t_step / nrhs)}
+            s64.close()
+            del v64
+        # --- end to end through the public API with host buffers
+        u_host = torch.empty((nrhs,) + s.shape, dtype=torch.complex128).pin_memory()
+        e2e_t = []
+        src_bytes = len(sources) * (3 * 4 + 2 * 8)
+        for it in range(1 + args.e2e_steps if args.e2e_steps > 0 else 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cd = c_host.to("cuda", non_blocking=True)
+            se = hz.Solver(w.n, w.n_pml, w.h, w.omega, cd, params=params, max_nrhs=nrhs)
+            _, _, st = se.helmholtz_solve(sources, v_out=v, u_out=u)
+            u_host.copy_(u, non_blocking=True)
+            torch.cuda.synchronize()
+            se.close()
+            if it >= 1:
+                e2e_t.append(time.perf_counter() - t0)
+        te = statistics.median(e2e_t) if e2e_t else float("nan")
+        result["e2e"] = None if not e2e_t else {"value": N * nrhs * st["pc_calls"] / te / 1e9, "unit": "GUpdates/s",
+                         "h2d_bytes_per_step": int(c_host.numel() * 8 + src_bytes),
+                         "d2h_bytes_per_step": int(u_host.numel() * 16), "time_to_solution_s": te,
+                         "includes": "H2D velocity, hz_create (set-up), solve, D2H of u, hz_destroy"}
+        # --- CPU oracle baseline (bounded sample)
+        if not args.no_cpu:
+            cv, cdt, cores, desc = oracle_sample(w.name)
+            result["cpu_baseline"] = {"value": cv, "unit": "GUpdates/s", "cores": cores, "kind": "oracle",
+                                      "sample": desc}
+        result["context"] = ("paper: 18.1 s on 64 A100 for ~340 wavelengths/direction (2048^3, tol 1e-4); "
+                             "not comparable hardware or workload")
+        print(json.dumps(result), flush=True)
+    s.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="2", choices=["1", "2", "3"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,9 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
                     int table_rows, int max_nrhs, void* stream, hz_handle** out);
 hz_status hz_destroy(hz_handle* h);
 const char* hz_last_error(const hz_handle* h);
+/* Number of kernels this library has launched in this process (each CUDA
+ * graph replay counts the kernels it contains).  Instrumentation only. */
+unsigned long long hz_kernel_launches(void);
 /* Device bytes hz_create would allocate for these sizes. */
 hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int max_nrhs, size_t* bytes);
 /* Replace the solver parameters (e.g. tolerance); cached CUDA graphs are dropped. */

@@ -24,7 +24,7 @@ _STATUS = {0: "HZ_OK", 1: "HZ_EINVAL", 2: "HZ_ENOMEM", 3: "HZ_ECUDA", 4: "HZ_ENO
 
 EXPORTED = ["hz_default_params", "hz_create", "hz_destroy", "hz_last_error", "hz_workspace_bytes",
             "hz_set_params", "iofd_coeffs", "iofd_apply", "threegrid_precond", "helmholtz_solve",
-            "helmholtz_adjoint_grad"]
+            "helmholtz_adjoint_grad", "hz_kernel_launches"]
 
 
 class HzGrid(ctypes.Structure):
@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hz_last_error.restype = ctypes.c_char_p
     lib.hz_workspace_bytes.argtypes = [P(HzGrid), P(HzParams), ctypes.c_int, P(ctypes.c_size_t)]
     lib.hz_set_params.argtypes = [vp, P(HzParams)]
+    lib.hz_kernel_launches.argtypes = []
+    lib.hz_kernel_launches.restype = ctypes.c_ulonglong
     lib.iofd_coeffs.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.iofd_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.threegrid_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
@@ -84,7 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helmholtz_adjoint_grad.argtypes = [vp, P(HzSource), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
                                            P(ctypes.c_double), P(ctypes.c_double), vp, P(HzStats)]
     for name in EXPORTED:
-        if name not in ("hz_default_params", "hz_last_error"):
+        if name not in ("hz_default_params", "hz_last_error", "hz_kernel_launches"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -241,6 +243,11 @@ class Solver:
             rec.shape[0], dv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(J),
             ctypes.c_void_p(g.data_ptr()), ctypes.byref(stats)))
         return J.value, g, stats.as_dict()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libhz.so so far in this process."""
+    return int(load_library().hz_kernel_launches())
 
 
 def workspace_bytes(n, n_pml, h, omega, params=None, max_nrhs=1, gamma_max=1.119058) -> int:

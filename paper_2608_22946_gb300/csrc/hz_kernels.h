@@ -4,9 +4,16 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
+
 #include "hz_common.cuh"
 
 namespace hz {
+
+// Kernels launched by this library in the process (instrumentation for the
+// benchmark's launch count; graph replays add their kernel-node count).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 enum StencilMode { M_APPLY = 0, M_RESID = 1, M_J2 = 2, M_JSWEEP = 3, M_J1 = 4 };
 enum StencilOp { OP_AB = 0, OP_Q = 1 };

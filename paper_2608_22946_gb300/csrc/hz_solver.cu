@@ -27,6 +27,8 @@
 
 using namespace hz;
 
+std::atomic<unsigned long long> hz::g_launches{0};
+
 namespace {
 
 struct Fail {
@@ -137,7 +139,7 @@ struct hz_handle {
   double* red_partial = nullptr;
   unsigned* red_count = nullptr;
   double *s_nrm = nullptr, *s_root = nullptr, *s_inv = nullptr;
-  std::map<std::tuple<int, int, int, const void*, void*>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, int, int, const void*, void*>, std::pair<cudaGraphExec_t, unsigned long long>> graphs;
   double t_setup = 0;
   bool use_graphs = true;
 };
@@ -470,7 +472,7 @@ void precond_enqueue(hz_handle* H, const cx<R>* r, cx<R>* z, int nrhs, bool adj)
 }
 
 void drop_graphs(hz_handle* H) {
-  for (auto& kv : H->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : H->graphs) cudaGraphExecDestroy(kv.second.first);
   H->graphs.clear();
 }
 
@@ -485,7 +487,8 @@ void precond(hz_handle* H, const cx<R>* r, cx<R>* z, int nrhs, bool adj) {
   auto it = H->graphs.find(key);
   if (it == H->graphs.end()) {
     if (H->graphs.size() >= 64) drop_graphs(H);  // bound the cache (new buffers each call)
-    cudaGraph_t graph;
+    cudaGraph_t graph = nullptr;
+    const unsigned long long c0 = g_launches.load();
     HZ_CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
     try {
       precond_enqueue<R>(H, r, z, nrhs, adj);
@@ -493,16 +496,20 @@ void precond(hz_handle* H, const cx<R>* r, cx<R>* z, int nrhs, bool adj) {
       cudaStreamEndCapture(H->st, &graph);
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
+      g_launches.store(c0);
       throw;
     }
     HZ_CK(cudaStreamEndCapture(H->st, &graph));
+    const unsigned long long nodes = g_launches.load() - c0;  // kernels recorded, not run
+    g_launches.store(c0);
     cudaGraphExec_t exec;
     cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     HZ_CK(e);
-    it = H->graphs.emplace(key, exec).first;
+    it = H->graphs.emplace(key, std::make_pair(exec, nodes)).first;
   }
-  HZ_CK(cudaGraphLaunch(it->second, H->st));
+  HZ_CK(cudaGraphLaunch(it->second.first, H->st));
+  count_launch(it->second.second);
 }
 
 // ----------------------------------------------------------------------------
@@ -865,6 +872,8 @@ void hz_default_params(hz_params* p) {
 }
 
 const char* hz_last_error(const hz_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+unsigned long long hz_kernel_launches(void) { return g_launches.load(); }
 
 hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int max_nrhs, size_t* bytes) {
   if (!grid || !params || !bytes || max_nrhs < 1) return HZ_EINVAL;

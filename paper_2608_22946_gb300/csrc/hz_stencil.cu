@@ -576,6 +576,7 @@ static void launch_fwd_t(const StencilCall<R>& c, cudaStream_t s) {
   int zb = choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
   int tiles_x = (L.nx + TX - 1) / TX;
   dim3 grid(tiles_x * c.nrhs, (L.ny + TY - 1) / TY, (L.nz + zb - 1) / zb);
+  count_launch();
   k_fwd<R, MODE, OP><<<grid, dim3(TX, TY), 0, s>>>(c, zb, tiles_x);
 }
 
@@ -587,6 +588,7 @@ static void launch_adj_t(const StencilCall<R>& c, cudaStream_t s) {
   int tiles_x = (L.nx + TX - 1) / TX;
   dim3 grid(tiles_x * c.nrhs, (L.ny + TY - 1) / TY, (L.nz + zb - 1) / zb);
   size_t smem = 3 * PLANE * (sizeof(cx<R>) + NP * sizeof(R)) + kMaxSeg * kNumFn * 4 * sizeof(R);
+  count_launch();
   k_adj<R, MODE, OP><<<grid, dim3(TX, TY), smem, s>>>(c, zb, tiles_x);
 }
 
@@ -595,6 +597,7 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
   if (mode == M_J1) {
     long long n = c.lv.N * c.nrhs;
     int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    count_launch();
     k_j1<R><<<blocks, 256, 0, s>>>(c, adjoint ? 1 : 0);
     return;
   }

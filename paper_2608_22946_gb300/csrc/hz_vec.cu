@@ -83,12 +83,14 @@ __global__ void k_prolong_add(const cx<R>* __restrict__ c, const cx<R>* __restri
 template <class R>
 void launch_restrict(const cx<R>* fine, cx<R>* coarse, int nxf, int nyf, int nzf, int nrhs, cudaStream_t s) {
   long long nc = (long long)((nxf - 1) / 2 + 1) * ((nyf - 1) / 2 + 1) * ((nzf - 1) / 2 + 1) * nrhs;
+  count_launch();
   k_restrict<R><<<vec_blocks(nc), VB, 0, s>>>(fine, coarse, nxf, nyf, nzf, nrhs);
 }
 template <class R>
 void launch_prolong_add(const cx<R>* coarse, const cx<R>* base, cx<R>* fine, int nxf, int nyf, int nzf, int nrhs,
                         cudaStream_t s) {
   long long nf = (long long)nxf * nyf * nzf * nrhs;
+  count_launch();
   k_prolong_add<R><<<vec_blocks(nf), VB, 0, s>>>(coarse, base, fine, nxf, nyf, nzf, nrhs);
 }
 
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
 template <class R, int KN>
 static void cgs_kn(const KrylovCall& k, const cx<R>* V, cx<R>* w, const CgsArgs& a, cudaStream_t s) {
   dim3 grid(vec_blocks(k.n), k.nrhs);
+  count_launch();
   k_cgs<R, KN><<<grid, VB, 0, s>>>(V, w, a);
 }
 
@@ -287,6 +290,7 @@ __global__ void k_scale(const cx<R>* __restrict__ w, cx<R>* __restrict__ out, co
 }
 template <class R>
 void launch_scale(const cx<R>* w, cx<R>* out, const double* scale, int n, int nrhs, cudaStream_t s) {
+  count_launch();
   k_scale<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(w, out, scale, n, nrhs);
 }
 
@@ -307,6 +311,7 @@ __global__ void k_combine(const cx<R>* __restrict__ Z, long long zstride, int kn
 template <class R>
 void launch_combine(const cx<R>* Z, long long zstride, int kn, const double* y, int ld, const cx<R>* x0, cx<R>* x,
                     int n, int nrhs, cudaStream_t s) {
+  count_launch();
   k_combine<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(Z, zstride, kn, y, ld, x0, x, n);
 }
 
@@ -318,6 +323,7 @@ __global__ void k_axpy(const cx<R>* __restrict__ x, cx<R>* __restrict__ y, R ar,
 }
 template <class R>
 void launch_axpy(const cx<R>* x, cx<R>* y, double ar, double ai, long long n, cudaStream_t s) {
+  count_launch();
   k_axpy<R><<<vec_blocks(n), VB, 0, s>>>(x, y, (R)ar, (R)ai, n);
 }
 template <class R>
@@ -327,6 +333,7 @@ __global__ void k_copy(const cx<R>* __restrict__ x, cx<R>* __restrict__ y, long 
 }
 template <class R>
 void launch_copy(const cx<R>* x, cx<R>* y, long long n, cudaStream_t s) {
+  count_launch();
   k_copy<R><<<vec_blocks(n), VB, 0, s>>>(x, y, n);
 }
 template <class R>
@@ -336,6 +343,7 @@ __global__ void k_zero(cx<R>* y, long long n) {
 }
 template <class R>
 void launch_zero(cx<R>* y, long long n, cudaStream_t s) {
+  count_launch();
   k_zero<R><<<vec_blocks(n), VB, 0, s>>>(y, n);
 }
 
@@ -350,6 +358,7 @@ __global__ void k_c128_to_c64(const cx<double>* __restrict__ in, cx<float>* __re
 }
 void launch_c128_to_c64_scaled(const cx<double>* in, cx<float>* out, const double* scale, int n, int nrhs,
                                cudaStream_t s) {
+  count_launch();
   k_c128_to_c64<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(in, out, scale, n);
 }
 __global__ void k_add_c64_to_c128(const cx<float>* __restrict__ d, cx<double>* __restrict__ x,
@@ -365,6 +374,7 @@ __global__ void k_add_c64_to_c128(const cx<float>* __restrict__ d, cx<double>* _
 }
 void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const double* scale, int n, int nrhs,
                                    cudaStream_t s) {
+  count_launch();
   k_add_c64_to_c128<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(d, x, scale, n);
 }
 
@@ -438,6 +448,7 @@ __global__ void k_lsq(const double* H, const double* beta, double* y, int m, int
   givens_lsq(H + (size_t)r * m * (m + 1) * 2, m + 1, m, beta[r], y + (size_t)r * ld * 2);
 }
 void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s) {
+  count_launch();
   k_lsq<<<(nrhs + 31) / 32, 32, 0, s>>>(H, beta, y, m, ld, nrhs);
 }
 
@@ -536,12 +547,18 @@ void launch_gram_lsq(const cx<R>* P, long long pstride, int kn, int n, int nrhs,
                      const Reduce& red, cudaStream_t s) {
   dim3 grid(vec_blocks(n), nrhs);
   switch (kn) {
-    case 2: k_gram<R, 2><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
-    case 3: k_gram<R, 3><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
-    case 4: k_gram<R, 4><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
-    case 5: k_gram<R, 5><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
-    case 6: k_gram<R, 6><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
-    case 7: k_gram<R, 7><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 2: count_launch();
+      k_gram<R, 2><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 3: count_launch();
+      k_gram<R, 3><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 4: count_launch();
+      k_gram<R, 4><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 5: count_launch();
+      k_gram<R, 5><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 6: count_launch();
+      k_gram<R, 6><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
+    case 7: count_launch();
+      k_gram<R, 7><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
     default: break;
   }
 }
@@ -567,6 +584,7 @@ template <class R>
 void launch_setup_kappa(const double* c, int nxf, int nyf, int nzf, int n_pml, int stride, double omega,
                         double ell, R* kappa, cudaStream_t s) {
   long long n = (long long)((nxf - 1) / stride + 1) * ((nyf - 1) / stride + 1) * ((nzf - 1) / stride + 1);
+  count_launch();
   k_setup_kappa<R><<<vec_blocks(n), VB, 0, s>>>(c, nxf, nyf, nzf, n_pml, stride, omega, ell, kappa);
 }
 
@@ -583,6 +601,7 @@ __global__ void k_point_sources(const int* idx3, const double* amp, int nsrc, in
 template <class R>
 void launch_point_sources(const int* idx3, const double* amp, int nsrc, int nx, int ny, int nz, double scale,
                           cx<R>* f, cudaStream_t s) {
+  count_launch();
   k_point_sources<R><<<(nsrc + 63) / 64, 64, 0, s>>>(idx3, amp, nsrc, nx, ny, nz, scale, f);
 }
 
@@ -596,6 +615,7 @@ __global__ void k_gather(const cx<R>* u, const int* rec, int nrec, int n, int nr
 template <class R>
 void launch_gather(const cx<R>* u, const int* rec, int nrec, int n, int nrhs, cx<double>* out, cudaStream_t s) {
   long long t = (long long)nrec * nrhs;
+  count_launch();
   k_gather<R><<<(int)((t + 255) / 256), 256, 0, s>>>(u, rec, nrec, n, nrhs, out);
 }
 // receivers are distinct nodes, so the scatter has no write conflicts
@@ -609,6 +629,7 @@ __global__ void k_scatter(const cx<double>* vals, const int* rec, int nrec, int 
 template <class R>
 void launch_scatter(const cx<double>* vals, const int* rec, int nrec, int n, int nrhs, cx<R>* out, cudaStream_t s) {
   long long t = (long long)nrec * nrhs;
+  count_launch();
   k_scatter<R><<<(int)((t + 255) / 256), 256, 0, s>>>(vals, rec, nrec, n, nrhs, out);
 }
 
@@ -709,6 +730,7 @@ __global__ void k_gradient(LevelView<double> L, TableView<double> T, double omeg
 void launch_gradient(const LevelView<double>& lv, const TableView<double>& tab, double omega_h,
                      const cx<double>* v, const cx<double>* lam, const cx<double>* f, const cx<double>* rres,
                      int nrhs, double* g_ext, cudaStream_t s) {
+  count_launch();
   k_gradient<<<vec_blocks(lv.N), VB, 0, s>>>(lv, tab, omega_h, v, lam, f, rres, nrhs, g_ext);
 }
 
@@ -732,6 +754,7 @@ __global__ void k_fold_pml(const double* __restrict__ ge, double* __restrict__ g
   }
 }
 void launch_fold_pml(const double* g_ext, double* g, int nx, int ny, int nz, int n_pml, cudaStream_t s) {
+  count_launch();
   k_fold_pml<<<vec_blocks((long long)nx * ny * nz), VB, 0, s>>>(g_ext, g, nx, ny, nz, n_pml);
 }
 
@@ -749,6 +772,7 @@ __global__ void k_shell_coeffs(LevelView<double> L, TableView<double> T, double*
   }
 }
 void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& tab, double* out, cudaStream_t s) {
+  count_launch();
   k_shell_coeffs<<<vec_blocks(lv.N), VB, 0, s>>>(lv, tab, out);
 }
 
