@@ -39,6 +39,13 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -204,12 +211,15 @@ def run_gpu(args):
     params = hz.default_params(tol=1e-6, precision=hz.HZ_C64)
     c_host = torch.from_numpy(w.c.reshape(-1)).pin_memory()
     c_dev = c_host.to("cuda", non_blocking=True)
+    log(f"workload {w.name} n={w.n} ready")
     s = hz.Solver(w.n, w.n_pml, w.h, w.omega, c_dev, params=params, max_nrhs=nrhs)
     N = w.N
     v = torch.empty((nrhs,) + s.shape, dtype=torch.complex128, device="cuda")
     u = torch.empty_like(v)
-    for _ in range(args.warmup):
-        s.helmholtz_solve(sources, v_out=v, u_out=u)
+    for it in range(args.warmup):
+        _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u)
+        log(f"warmup {it}: pc={st['pc_calls']} passes={st['refine_passes']} rel={st['rel_res']:.2e} "
+            f"t={st['t_solve']:.3f}s")
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     barrier(pg, dev)
@@ -226,6 +236,7 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(pg, dev)
+    log(f"timed: {[round(st['t_solve'], 4) for st in stats]}")
     launches = hz.kernel_launches() - l0
     t_step = ev0.elapsed_time(ev1) / 1000.0 / args.steps
     t_step = allreduce_max(pg, t_step)
@@ -271,6 +282,7 @@ def run_gpu(args):
         if os.path.exists(tf):
             with open(tf) as f:
                 traffic = json.load(f).get("bytes_per_launch_fine_288")
+        log(f"stencil apply {1000 * t_k:.3f} ms")
         result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                               "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                               "kernel": "k_fwd<float,APPLY,AB> (A_h, complex64, fine grid)",
@@ -287,6 +299,7 @@ def run_gpu(args):
             _, _, st64 = s64.helmholtz_solve(sources[:1], v_out=v64, want_u=False)
             torch.cuda.synchronize()
             t64 = time.perf_counter() - t0
+            log(f"fp64 solve {t64:.2f}s pc={st64['pc_calls']} rel={st64['rel_res']:.2e}")
             err = float(torch.linalg.vector_norm(v[0] - v64[0]) / torch.linalg.vector_norm(v64[0]))
             result["fp64_solve"] = {"time_to_solution_s": t64, "pc_calls": st64["pc_calls"],
                                     "rel_res": st64["rel_res"], "mixed_vs_fp64_rel_l2": err,
@@ -309,6 +322,7 @@ def run_gpu(args):
             if it >= 1:
                 e2e_t.append(time.perf_counter() - t0)
         te = statistics.median(e2e_t) if e2e_t else float("nan")
+        log(f"e2e {e2e_t}")
         result["e2e"] = None if not e2e_t else {"value": N * nrhs * st["pc_calls"] / te / 1e9, "unit": "GUpdates/s",
                          "h2d_bytes_per_step": int(c_host.numel() * 8 + src_bytes),
                          "d2h_bytes_per_step": int(u_host.numel() * 16), "time_to_solution_s": te,
@@ -316,6 +330,7 @@ def run_gpu(args):
         # --- CPU oracle baseline (bounded sample)
         if not args.no_cpu:
             cv, cdt, cores, desc = oracle_sample(w.name)
+            log(f"oracle sample {cdt:.1f}s")
             result["cpu_baseline"] = {"value": cv, "unit": "GUpdates/s", "cores": cores, "kind": "oracle",
                                       "sample": desc}
         result["context"] = ("paper: 18.1 s on 64 A100 for ~340 wavelengths/direction (2048^3, tol 1e-4); "
@@ -324,6 +339,36 @@ def run_gpu(args):
     s.close()
     if pg is not None:
         pg.destroy_process_group()
+
+
+def run_stencil_only(args):
+    """Time the fine-grid complex64 A_h apply alone (the kernel the roofline
+    line reports), K launches after 3 warm-ups, inputs larger than L2."""
+    import torch
+    import hz_workloads as W
+    import paper_2608_22946_gb300 as hz
+    w = {"2": W.gaussian_lens, "1": W.homogeneous, "3": W.layered_inclusion}[args.config]()
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=1)
+    x = torch.randn((1,) + s.shape, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0 / args.steps
+    pk, _ = peaks()
+    gbs = 20 * w.N / t / 1e9
+    print(json.dumps({"kernel": "k_fwd A_h complex64", "workload": w.name, "n": w.n, "nodes": w.N,
+                      "ms": 1000 * t, "gupdates_per_s": w.N / t / 1e9, "gb_per_s": gbs,
+                      "frac_hbm": gbs / pk["hbm_gbs"]}), flush=True)
+    s.close()
 
 
 def main():
@@ -336,8 +381,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--stencil-only", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.stencil_only:
+        run_stencil_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -167,6 +167,32 @@ def make_problem(c, n_pml, h, omega, gamma_max=1.119058, tables=None, nlevels=3)
     return Problem(n, n_pml, h, omega, gamma_max, c_ext, levels, tables)
 
 
+class PointKappa:
+    """kappa = omega ell / c_ext evaluated on demand at node indices, for grids
+    too large to hold whole; c_ext copies the nearest physical node (Sec. 2.1)
+    and level L samples fine node 2^L j (Sec. 3.1)."""
+
+    def __init__(self, c, n_pml, omega, ell, stride):
+        self.c, self.n_pml, self.omega, self.ell, self.f = c, n_pml, omega, ell, stride
+        self.n = tuple(s - 1 for s in c.shape)
+
+    def __getitem__(self, key):
+        idx = []
+        for i, m in zip(key, self.n):
+            idx.append(np.clip(np.asarray(i, dtype=np.int64) * self.f, self.n_pml, m - self.n_pml))
+        return self.omega * self.ell / np.asarray(self.c[idx[0], idx[1], idx[2]], dtype=np.float64)
+
+
+def make_level_points(c, n_pml, h, omega, gamma_max=1.119058, L=0) -> Level:
+    """Level L whose kappa is evaluated only where indexed (use with
+    ``row_coefficient_points``)."""
+    f = 1 << L
+    n = tuple((s - 1) // f for s in c.shape)
+    pL = n_pml // f
+    pml = tuple(pml_1d(m, pL, gamma_max) for m in n)
+    return Level(L, n, pL, h * f, PointKappa(c, n_pml, omega, h * f, f), pml)
+
+
 # ----------------------------------------------------------------------------
 # Row coefficients A_i(delta) of the PML-stretched IOFD operator
 # ----------------------------------------------------------------------------
@@ -212,6 +238,37 @@ def row_coefficient(level: Level, tables: Tables, delta, shift_sigma: float = 0.
     m = sum(1 for o in delta if o != 0)
     mass = (1.0 + 1j * shift_sigma) * mass_scale * level.kappa ** 2 * mw[m]
     return (-stiff - mass) / level.ell ** 2
+
+
+def row_coefficient_points(level: Level, tables: Tables, delta, iz, iy, ix, shift_sigma: float = 0.0):
+    """A_i(delta) of ``row_coefficient`` at the nodes (iz, iy, ix) only (for
+    sampled checks on grids too large to evaluate whole): the same
+    tensor-product row with the PML factors of each node's own coordinates."""
+    iz, iy, ix = (np.asarray(v, dtype=np.int64) for v in (iz, iy, ix))
+    kap = level.kappa[iz, iy, ix]
+    eta = np.minimum(kap / (2.0 * math.pi), ETA_MAX)
+    a, _ = hermite(tables.s, tables.alpha, tables.dalpha, eta)
+    a1, a2, a3, a4, a5 = (a[..., j] for j in range(5))
+    tw = {0: a4, 1: a5 / 4.0, 2: (1.0 - a4 - a5) / 4.0}
+    mw = {0: a1, 1: a2 / 6.0, 2: a3 / 12.0, 3: (1.0 - a1 - a2 - a3) / 8.0}
+    coords = (iz, iy, ix)
+    stiff = np.zeros(kap.shape, dtype=np.complex128)
+    for axis in range(3):
+        others = [delta[k] for k in range(3) if k != axis]
+        nnz_t = sum(1 for o in others if o != 0)
+        stiff = stiff + _pml_d(level, axis, delta[axis])[coords[axis]] * tw[nnz_t]
+    m = sum(1 for o in delta if o != 0)
+    mass = (1.0 + 1j * shift_sigma) * kap ** 2 * mw[m]
+    return (-stiff - mass) / level.ell ** 2
+
+
+def apply_points(level: Level, tables: Tables, x_at, iz, iy, ix, shift_sigma: float = 0.0):
+    """(A x)_i at the nodes (iz, iy, ix); ``x_at(dz, dy, dx)`` returns x at the
+    neighbours (zero outside the grid)."""
+    y = 0.0
+    for d in OFFSETS:
+        y = y + row_coefficient_points(level, tables, d, iz, iy, ix, shift_sigma) * x_at(*d)
+    return y
 
 
 def shift_field(v: np.ndarray, delta) -> np.ndarray:

@@ -84,7 +84,12 @@ void launch_combine(const cx<R>* Z, long long zstride, int kn, const double* y, 
 
 // Small least-squares min || beta e1 - H y || per rhs (H: (m+1) x m, column-major
 // complex double, leading dim m+1, per rhs stride (m+1)*m); y rows of length ld.
-void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s);
+void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s,
+                bool single);
+// w <- (w - sum_k coef[r][k] V_k) * scale[r]: last Gram-Schmidt pass fused with the normalisation
+template <class R>
+void launch_update_scale(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coef, const double* scale,
+                         cudaStream_t s);
 
 // Gram matrix of kn vectors, Cholesky, and the CA-GMRES least-squares solve
 // min || p_0 - sum_{k>=1} y_{k-1} p_k ||; writes y (kn-1 entries per rhs).

@@ -368,13 +368,14 @@ void arnoldi_orth(hz_handle* H, int L, int nrhs, cx<R>* V, int j, double* Hm, in
   k.ld = m + 1;
   cx<R>* w = V + (j + 1) * k.vstride;
   Reduce red = reducer(H, nullptr);
+  // pass 1: h1 = V^H w
   launch_cgs<R>(k, V, w, nullptr, false, true, false, W.coef1, nullptr, EPI_ARNOLDI_FIRST, Hm, j, nullptr, nullptr,
                 red, H->st);
-  launch_cgs<R>(k, V, w, W.coef1, true, true, false, W.coef2, nullptr, EPI_ARNOLDI_SECOND, Hm, j, nullptr,
-                nullptr, red, H->st);
-  launch_cgs<R>(k, V, w, W.coef2, true, false, true, nullptr, nullptr, EPI_NORMALISE, Hm, j, scale, nullptr, red,
-                H->st);
-  launch_scale<R>(w, w, scale, k.n, nrhs, H->st);
+  // pass 2: w -= V h1, then h2 = V^H w and ||w||^2 -> column += h2, subdiagonal, 1/norm
+  launch_cgs<R>(k, V, w, W.coef1, true, true, true, W.coef2, nullptr, EPI_ARNOLDI_SECOND, Hm, j, scale, nullptr,
+                red, H->st);
+  // pass 3: v_{j+1} = (w - V h2) / norm
+  launch_update_scale<R>(k, V, w, W.coef2, scale, H->st);
   HZ_LAUNCHED();
 }
 
@@ -406,7 +407,7 @@ void gmres_cycle(hz_handle* H, int L, bool adj, const cx<R>* g, const cx<R>* x0,
     apply<R>(H, L, false, adj, Z + j * vs, V + (j + 1) * vs, nrhs);
     arnoldi_orth<R>(H, L, nrhs, V, j, Hm, m, scale);
   }
-  launch_lsq(Hm, beta, y, m, m + 1, nrhs, H->st);
+  launch_lsq(Hm, beta, y, m, m + 1, nrhs, H->st, sizeof(R) == sizeof(float));
   launch_combine<R>(Z, vs, m, y, m + 1, x0, x, n, nrhs, H->st);
   HZ_LAUNCHED();
 }
@@ -658,13 +659,19 @@ std::vector<double> host_copy(const double* d, int n, cudaStream_t st) {
 // ----------------------------------------------------------------------------
 // outer FGMRES(m_out) with FP64 Givens on the host (Sec. 3.3, Table 4)
 // ----------------------------------------------------------------------------
+// With `inner` set (the complex64 correction solve of the refinement loop) a
+// cycle whose Arnoldi estimate reaches tol ends the solve without a further
+// true residual, and the solve also ends when a restart cycle no longer
+// reduces the true residual by 10%: the FP64 refinement loop measures and
+// corrects what complex64 cannot resolve.
 template <class R>
 double outer_fgmres(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, const std::vector<double>& bn,
-                    double tol, int max_pc, int& pc) {
+                    double tol, int max_pc, int& pc, bool inner = false) {
   Work<R>& W = Sel<R>::w(H);
   const int m = H->p.m_out, ld = m + 1;
   const long long N = H->lev[0].N, vs = N * nrhs;
-  double relmax = 0.0;
+  double relmax = 0.0, prev_rel = HUGE_VAL;
+  bool est_converged = false;
   for (;;) {
     resid<R>(H, 0, false, adj, b, x, W.Vo, nrhs, reducer(H, W.nrm, W.beta_o, W.scale_o));
     std::vector<double> beta = host_copy(W.beta_o, nrhs, H->st);
@@ -674,6 +681,8 @@ double outer_fgmres(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, 
       relmax = std::max(relmax, bn[r] > 0 ? beta[r] / bn[r] : 0.0);
     }
     if (relmax <= tol || pc >= max_pc) break;
+    if (inner && relmax > 0.9 * prev_rel) break;  // complex64 stagnation: hand back to the refinement
+    prev_rel = relmax;
     launch_scale<R>(W.Vo, W.Vo, W.scale_o, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
     using C = std::complex<double>;
@@ -723,6 +732,7 @@ double outer_fgmres(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, 
         if (nb == 0.0) breakdown = true;
       }
       k = j + 1;
+      est_converged = all_conv;
       if (all_conv || breakdown || pc >= max_pc) break;
     }
     std::vector<double> yh((size_t)nrhs * LDMAX * 2, 0.0);
@@ -742,6 +752,7 @@ double outer_fgmres(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, 
     HZ_CK(cudaMemcpyAsync(W.yo, yh.data(), (size_t)nrhs * ld * 2 * sizeof(double), cudaMemcpyHostToDevice, H->st));
     launch_combine<R>(W.Zo, vs, k, W.yo, ld, x, x, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
+    if (inner && (est_converged || pc >= max_pc)) break;
   }
   return relmax;
 }
@@ -792,7 +803,7 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     std::vector<double> one(nrhs);
     for (int r = 0; r < nrhs; ++r) one[r] = rn[r] > 0 ? 1.0 : 0.0;
     double inner = std::max(p.inner_tol, need);
-    outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, inner, p.max_pc, o.pc);
+    outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, inner, p.max_pc, o.pc, true);
     launch_add_c64_to_c128_scaled(H->x64, x, H->s_root, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
   }

@@ -35,7 +35,8 @@ namespace hz {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int PW = TX + 2, PH = TY + 2, PLANE = PW * PH;
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 6;   // shared-memory plane ring
+constexpr int PREF = 5;     // planes in flight ahead of the one consumed (NSTAGE - 1)
 
 // ----------------------------------------------------------------------------
 // cp.async (zero fill when pred is false; the source address is then unused)
@@ -153,13 +154,65 @@ __device__ __forceinline__ cx<R> ldc(const cx<R>* p) { return *p; }
 // ----------------------------------------------------------------------------
 // forward kernel body
 // ----------------------------------------------------------------------------
+// alpha_1 and alpha_4 only (the diagonal needs no more)
+template <class R>
+__device__ __forceinline__ void table_a1a4(const R* __restrict__ tab, int nseg, R ds, R inv_ds, R eta, R& a1, R& a4) {
+  int seg = (int)(eta * inv_ds);
+  seg = seg < 0 ? 0 : (seg > nseg - 1 ? nseg - 1 : seg);
+  R u = eta - (R)seg * ds;
+  const R* c = tab + seg * kNumFn * 4;
+  a1 = c[0] + u * (c[1] + u * (c[2] + u * c[3]));
+  a4 = c[12] + u * (c[13] + u * (c[14] + u * c[15]));
+}
+
+// Which tiles a launch covers.  mode 0: the rectangle of tiles starting at
+// (tx0, ty0), ntx wide, gridDim.y high; mode 1: every tile of the TXT x TYT
+// tiling outside the rectangle [txa, txb] x [tya, tyb].  Blocks of all the
+// launches of one operator application share one numbering (bid_offset,
+// nblk_total) so that a fused grid reduction spans them.
+struct TileMap {
+  int mode = 0;
+  int tx0 = 0, ty0 = 0, ntx = 1;
+  int TXT = 1, TYT = 1, txa = 0, txb = -1, tya = 0, tyb = -1;
+  int bid_offset = 0, nblk_total = 1;
+};
+
+__device__ __forceinline__ void decode_tile(const TileMap& m, int nrhs, int& rhs, int& tile_x, int& tile_y,
+                                            unsigned& bid) {
+  rhs = blockIdx.x % nrhs;
+  const int t = blockIdx.x / nrhs;
+  if (m.mode == 0) {
+    tile_x = m.tx0 + t;
+    tile_y = m.ty0 + blockIdx.y;
+    bid = (unsigned)(m.bid_offset + t + m.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
+  } else {
+    const int RW = m.txb - m.txa + 1, RH = m.tyb - m.tya + 1;
+    const int n_top = m.tya * m.TXT, per_row = m.TXT - RW, n_mid = RH * per_row;
+    if (t < n_top) {
+      tile_y = t / m.TXT;
+      tile_x = t - tile_y * m.TXT;
+    } else if (t < n_top + n_mid) {
+      const int u = t - n_top;
+      tile_y = m.tya + u / per_row;
+      const int c = u - (tile_y - m.tya) * per_row;
+      tile_x = c < m.txa ? c : c + RW;
+    } else {
+      const int u = t - n_top - n_mid;
+      tile_y = m.tyb + 1 + u / m.TXT;
+      tile_x = u - (tile_y - m.tyb - 1) * m.TXT;
+    }
+    const int count = m.TXT * m.TYT - RW * RH;
+    bid = (unsigned)(m.bid_offset + t + count * blockIdx.z);
+  }
+}
+
 template <class R, int MODE, int OP, bool GEN>
-__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, int tiles_x, cx<R> (*sX)[PLANE],
-                                         R (*sK)[PLANE], cx<R>* sY1, const R* sTab, double* sRed) {
+__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, const TileMap& tm, int rhs, int tile_x,
+                                         int tile_y, unsigned bid, cx<R> (*sX)[PLANE], R (*sK)[PLANE], cx<R>* sY1,
+                                         const R* sTab, double* sRed) {
   const LevelView<R>& L = a.lv;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int rhs = blockIdx.x % a.nrhs, tile_x = blockIdx.x / a.nrhs;
-  const int x0 = tile_x * TX, y0 = blockIdx.y * TY;
+  const int x0 = tile_x * TX, y0 = tile_y * TY;
   const int zb0 = blockIdx.z * zblock;
   const int zb1 = min(zb0 + zblock, L.nz);
   const int nplanes = zb1 - zb0 + 2;
@@ -173,6 +226,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
   const cx<R> shift = a.mass_shift;
   const int nseg = a.tab.nseg;
   const R ds = a.tab.ds, inv_ds = a.tab.inv_ds;
+  const int zpl_lo = L.plain_lo[2], zpl_hi = L.plain_hi[2];
 
   // per-thread PML factors of its column (x, y fixed during the march)
   cx<R> abx = mkc<R>(1, 0), acx = mkc<R>(0, 0), aby = mkc<R>(1, 0), acy = mkc<R>(0, 0);
@@ -184,20 +238,41 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
     acy = L.achk[1][cyi];
   }
 
+  // this thread's (at most two) load slots in every plane, fixed for the march
+  const bool has1 = tid + NT < PLANE;
+  int li0 = tid, li1 = tid + NT;
+  long long go0 = 0, go1 = 0;
+  bool in0, in1 = false;
+  {
+    int ly = li0 / PW, lx = li0 - ly * PW;
+    int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
+    in0 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
+    go0 = in0 ? (long long)qy * L.nx + qx : 0;
+    if (has1) {
+      ly = li1 / PW;
+      lx = li1 - ly * PW;
+      qx = x0 - 1 + lx;
+      qy = y0 - 1 + ly;
+      in1 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
+      go1 = in1 ? (long long)qy * L.nx + qx : 0;
+    }
+  }
   auto issue = [&](int z, int st) {
-    for (int i = tid; i < PLANE; i += NT) {
-      int ly = i / PW, lx = i - ly * PW;
-      int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
-      bool in = (z >= 0) && (z < L.nz) && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
-      long long off = in ? ((long long)z * plane_sz + (long long)qy * L.nx + qx) : 0;
-      cp_async<sizeof(cx<R>)>(&sX[st][i], X + off, in);
-      if (MODE == M_J2) cp_async<sizeof(R)>(&sK[st][i], L.kappa + off, in);
+    const bool zin = (z >= 0) && (z < L.nz);
+    const long long zo = zin ? (long long)z * plane_sz : 0;
+    const bool p0 = zin && in0, p1 = zin && in1;
+    cp_async<sizeof(cx<R>)>(&sX[st][li0], X + (p0 ? zo + go0 : 0), p0);
+    if (has1) cp_async<sizeof(cx<R>)>(&sX[st][li1], X + (p1 ? zo + go1 : 0), p1);
+    if (MODE == M_J2) {
+      cp_async<sizeof(R)>(&sK[st][li0], L.kappa + (p0 ? zo + go0 : 0), p0);
+      if (has1) cp_async<sizeof(R)>(&sK[st][li1], L.kappa + (p1 ? zo + go1 : 0), p1);
     }
     cp_commit();
   };
 
-  // prologue: planes 0, 1, 2 of the block (zb0-1 .. zb0+1)
-  for (int k = 0; k < 3; ++k) {
+  // prologue: PREF planes in flight (zb0-1 ...)
+#pragma unroll
+  for (int k = 0; k < PREF; ++k) {
     if (k < nplanes) issue(zb0 - 1 + k, k);
     else cp_commit();
   }
@@ -215,10 +290,10 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
   for (int k = 0; k < nplanes; ++k) {
     const int zk = zb0 - 1 + k;
     const int st = k % NSTAGE;
-    cp_wait<2>();
+    cp_wait<PREF - 1>();
     __syncthreads();
     {
-      int kk = k + 3;
+      const int kk = k + PREF;
       if (kk < nplanes) issue(zb0 - 1 + kk, kk % NSTAGE);
       else cp_commit();
     }
@@ -226,7 +301,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
     const cx<R>* P = sX[st];
     if (MODE == M_J2) {
       // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first sweep)
-      cx<R> abz = zin ? L.abar[2][zk] : mkc<R>(1, 0);
+      const cx<R> abz = zin ? L.abar[2][zk] : mkc<R>(1, 0);
       for (int e = tid; e < PLANE; e += NT) {
         // element e < NT is the thread's own column, the rest the halo ring
         int lx, ly;
@@ -234,23 +309,23 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
           lx = tx + 1;
           ly = ty + 1;
         } else {
-          int hsel = e - NT;  // 0 .. 2*PW + 2*TY - 1
+          const int hsel = e - NT;  // 0 .. 2*PW + 2*TY - 1
           if (hsel < PW) { lx = hsel; ly = 0; }
           else if (hsel < 2 * PW) { lx = hsel - PW; ly = PH - 1; }
           else if (hsel < 2 * PW + TY) { lx = 0; ly = hsel - 2 * PW + 1; }
           else { lx = PW - 1; ly = hsel - 2 * PW - TY + 1; }
         }
-        int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
-        int li = ly * PW + lx;
-        bool in = zin && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
+        const int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
+        const int li = ly * PW + lx;
+        const bool in = zin && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
         cx<R> y1 = mkc<R>(0, 0), dinv = mkc<R>(0, 0);
-        cx<R> g = P[li];
-        R kap = sK[st][li];
+        const cx<R> g = P[li];
+        const R kap = sK[st][li];
         if (in) {
-          R av[5];
-          table_eval<R, 0, 5>(sTab, nseg, ds, inv_ds, eta_star(kap), av);
-          cx<R> sab = L.abar[0][qx] + L.abar[1][qy] + abz;
-          cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (inv_ell2 * kap * kap * av[0]) * shift;
+          R a1, a4;
+          table_a1a4<R>(sTab, nseg, ds, inv_ds, eta_star(kap), a1, a4);
+          const cx<R> sab = L.abar[0][qx] + L.abar[1][qy] + abz;
+          const cx<R> D = inv_ell2 * ((R)2 * a4 * sab) - (inv_ell2 * kap * kap * a1) * shift;
           dinv = cinv(D);
           y1 = a.omega_j * (dinv * g);
         }
@@ -266,7 +341,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
       P = sY1;
     } else {
       if (active && zin) {
-        long long idx = (long long)zk * plane_sz + col;
+        const long long idx = (long long)zk * plane_sz + col;
         kap_cur = L.kappa[idx];
         if (MODE == M_RESID || MODE == M_JSWEEP) g_cur = G[idx];
         if (MODE == M_JSWEEP) xc_cur = P[(ty + 1) * PW + tx + 1];
@@ -278,7 +353,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
       const int z = zk - 1;
       const long long idx = (long long)z * plane_sz + col;
       cx<R> out;
-      if (OP == OP_Q) {
+      if constexpr (OP == OP_Q) {
         R bv[3];
         table_eval<R, 5, 3>(sTab, nseg, ds, inv_ds, eta_star(kap_prev), bv);
         if constexpr (!GEN) out = q_row(wm, w0, wp, bv);
@@ -286,12 +361,34 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
       } else {
         R av[5];
         table_eval<R, 0, 5>(sTab, nseg, ds, inv_ds, eta_star(kap_prev), av);
-        cx<R> abz = L.abar[2][z], acz = L.achk[2][z];
-        cx<R> Mv, Ls;
-        if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, abx, acx, aby, acy, abz, acz, Mv);
-        else Ls = stiff_mass(wm, w0, wp, av, abz, acz, Mv);
         const R mk = inv_ell2 * kap_prev * kap_prev;
-        cx<R> Hx = (-inv_ell2) * Ls - (mk * shift) * Mv;
+        cx<R> Hx, sab;
+        bool shell_row = false;
+        if constexpr (!GEN) {
+          if (z >= zpl_lo && z <= zpl_hi) {
+            // interior row: shell form of Eq. iofd-shell-form, stiffness and mass parts
+            const R a1 = av[0], a2 = av[1], a3 = av[2], a4 = av[3], a5 = av[4];
+            const R b = (R)1 - a4 - a5;
+            const cx<R> N1 = w0.e + (wm.c + wp.c);
+            const cx<R> N2 = w0.k + (wm.e + wp.e);
+            const cx<R> N3 = wm.k + wp.k;
+            const cx<R> Ls =
+                ((R)6 * a4) * w0.c + (a5 - a4) * N1 + ((R)0.5 * (b - a5)) * N2 + ((R)(-0.75) * b) * N3;
+            const cx<R> Ms = a1 * w0.c + (a2 * (R)(1.0 / 6.0)) * N1 + (a3 * (R)(1.0 / 12.0)) * N2 +
+                             (((R)1 - a1 - a2 - a3) * (R)0.125) * N3;
+            Hx = inv_ell2 * Ls - (mk * shift) * Ms;
+            sab = mkc<R>(3, 0);
+            shell_row = true;
+          }
+        }
+        if (!shell_row) {
+          const cx<R> abz = L.abar[2][z], acz = L.achk[2][z];
+          cx<R> Mv, Ls;
+          if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, abx, acx, aby, acy, abz, acz, Mv);
+          else Ls = stiff_mass(wm, w0, wp, av, abz, acz, Mv);
+          Hx = (-inv_ell2) * Ls - (mk * shift) * Mv;
+          sab = abx + aby + abz;
+        }
         if (MODE == M_APPLY) {
           out = Hx;
         } else if (MODE == M_RESID) {
@@ -300,8 +397,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
           out = xc_prev + a.omega_j * (dinv_prev * (g_prev - Hx));
           if (a.base) out += a.base[rhs * N + idx];
         } else {  // M_JSWEEP
-          cx<R> sab = abx + aby + abz;
-          cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (mk * av[0]) * shift;
+          const cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (mk * av[0]) * shift;
           out = xc_prev + a.omega_j * cdiv(g_prev - Hx, D);
         }
       }
@@ -319,8 +415,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
 
   if (MODE == M_RESID && a.red.out) {
     double s = block_sum(nrm2, sRed, tid, NT);
-    const unsigned nblk = (unsigned)(tiles_x * gridDim.y * gridDim.z);
-    const unsigned bid = (unsigned)(tile_x + tiles_x * (blockIdx.y + gridDim.y * blockIdx.z));
+    const unsigned nblk = (unsigned)tm.nblk_total;
     if (tid == 0) a.red.partial[(size_t)rhs * nblk + bid] = s;
     if (last_block_arrive(a.red.count + rhs, nblk, tid)) {
       double t = 0.0;
@@ -337,8 +432,10 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, in
   }
 }
 
-template <class R, int MODE, int OP>
-__global__ void __launch_bounds__(NT) k_fwd(StencilCall<R> a, int zblock, int tiles_x) {
+// PATH 0: interior (shell) tiles only; 1: PML tiles only; 2: either, chosen per tile.
+template <class R, int MODE, int OP, int PATH>
+__global__ void __launch_bounds__(NT, (PATH == 0 && sizeof(R) == 4) ? 4 : 1) k_fwd(StencilCall<R> a, int zblock,
+                                                                                   TileMap tm) {
   __shared__ cx<R> sX[NSTAGE][PLANE];
   __shared__ R sK[NSTAGE][(MODE == M_J2) ? PLANE : 1];
   __shared__ cx<R> sY1[(MODE == M_J2) ? PLANE : 1];
@@ -347,17 +444,21 @@ __global__ void __launch_bounds__(NT) k_fwd(StencilCall<R> a, int zblock, int ti
   const int tid = threadIdx.y * TX + threadIdx.x;
   for (int i = tid; i < a.tab.nseg * kNumFn * 4; i += NT) sTab[i] = a.tab.coef[i];
   // (visibility of sTab is ensured by the first __syncthreads of the march)
-  const LevelView<R>& L = a.lv;
-  const int tile_x = blockIdx.x / a.nrhs;
-  const int x0 = tile_x * TX, y0 = blockIdx.y * TY;
-  const bool plain = (OP == OP_Q) || ((x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) &&
-                                      (y0 >= L.plain_lo[1]) && (y0 + TY - 1 <= L.plain_hi[1]));
+  int rhs, tile_x, tile_y;
+  unsigned bid;
+  decode_tile(tm, a.nrhs, rhs, tile_x, tile_y, bid);
   R(*sKp)[PLANE] = reinterpret_cast<R(*)[PLANE]>(&sK[0][0]);  // only dereferenced in M_J2
-  if constexpr (OP == OP_Q) {
-    fwd_body<R, MODE, OP, false>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
+  if constexpr (OP == OP_Q || PATH == 0) {
+    fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
+  } else if constexpr (PATH == 1) {
+    fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
   } else {
-    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
-    else fwd_body<R, MODE, OP, true>(a, zblock, tiles_x, sX, sKp, sY1, sTab, sRed);
+    const LevelView<R>& L = a.lv;
+    const int x0 = tile_x * TX, y0 = tile_y * TY;
+    const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
+                       (y0 + TY - 1 <= L.plain_hi[1]);
+    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
+    else fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
   }
 }
 
@@ -570,14 +671,73 @@ static int choose_zblock(int nx, int ny, int nz, int nrhs) {
   return zb;
 }
 
+// Grids of at least this many nodes split interior and PML tiles into two
+// launches (each kernel then carries only its own path's registers); smaller
+// grids, where launch latency dominates, use one launch choosing per tile.
+constexpr long long kSplitNodes = 4LL << 20;
+
+struct FwdPlan {
+  int zb, nzb, TXT, TYT;
+  bool split;
+  int txa, txb, tya, tyb;
+};
+
+template <class R>
+static FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, int op) {
+  FwdPlan p;
+  p.zb = choose_zblock(L.nx, L.ny, L.nz, nrhs);
+  p.nzb = (L.nz + p.zb - 1) / p.zb;
+  p.TXT = (L.nx + TX - 1) / TX;
+  p.TYT = (L.ny + TY - 1) / TY;
+  // interior tile rectangle: tiles whose columns all lie in the PML-free range
+  p.txa = (L.plain_lo[0] + TX - 1) / TX;
+  p.txb = (L.plain_hi[0] + 1) / TX - 1;
+  p.tya = (L.plain_lo[1] + TY - 1) / TY;
+  p.tyb = (L.plain_hi[1] + 1) / TY - 1;
+  p.split = (op == OP_AB) && L.N >= kSplitNodes && p.txb >= p.txa && p.tyb >= p.tya;
+  return p;
+}
+
 template <class R, int MODE, int OP>
 static void launch_fwd_t(const StencilCall<R>& c, cudaStream_t s) {
   const LevelView<R>& L = c.lv;
-  int zb = choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
-  int tiles_x = (L.nx + TX - 1) / TX;
-  dim3 grid(tiles_x * c.nrhs, (L.ny + TY - 1) / TY, (L.nz + zb - 1) / zb);
+  const FwdPlan p = plan_fwd(L, c.nrhs, OP);
+  const int nblk_total = p.TXT * p.TYT * p.nzb;
+  if (!p.split) {
+    TileMap tm;
+    tm.mode = 0;
+    tm.ntx = p.TXT;
+    tm.nblk_total = nblk_total;
+    dim3 grid(p.TXT * c.nrhs, p.TYT, p.nzb);
+    count_launch();
+    k_fwd<R, MODE, OP, (OP == OP_Q) ? 0 : 2><<<grid, dim3(TX, TY), 0, s>>>(c, p.zb, tm);
+    return;
+  }
+  const int RW = p.txb - p.txa + 1, RH = p.tyb - p.tya + 1;
+  TileMap ti;
+  ti.mode = 0;
+  ti.tx0 = p.txa;
+  ti.ty0 = p.tya;
+  ti.ntx = RW;
+  ti.bid_offset = 0;
+  ti.nblk_total = nblk_total;
+  TileMap tp;
+  tp.mode = 1;
+  tp.TXT = p.TXT;
+  tp.TYT = p.TYT;
+  tp.txa = p.txa;
+  tp.txb = p.txb;
+  tp.tya = p.tya;
+  tp.tyb = p.tyb;
+  tp.bid_offset = RW * RH * p.nzb;
+  tp.nblk_total = nblk_total;
+  const int ncomp = p.TXT * p.TYT - RW * RH;
   count_launch();
-  k_fwd<R, MODE, OP><<<grid, dim3(TX, TY), 0, s>>>(c, zb, tiles_x);
+  k_fwd<R, MODE, OP, 0><<<dim3(RW * c.nrhs, RH, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, ti);
+  if (ncomp > 0) {
+    count_launch();
+    k_fwd<R, MODE, OP, 1><<<dim3(ncomp * c.nrhs, 1, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, tp);
+  }
 }
 
 template <class R, int MODE, int OP>

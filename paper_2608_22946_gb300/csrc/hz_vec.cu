@@ -20,6 +20,11 @@ static int vec_blocks(long long n) {
   long long b = (n + VB * 4 - 1) / (VB * 4);
   return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 8));
 }
+// reduction kernels use fewer, fuller blocks: fewer partial sums to combine
+static int red_blocks(long long n) {
+  long long b = (n + VB * 8 - 1) / (VB * 8);
+  return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 4));
+}
 
 // ----------------------------------------------------------------------------
 // transfers
@@ -95,19 +100,62 @@ void launch_prolong_add(const cx<R>* coarse, const cx<R>* base, cx<R>* fine, int
 }
 
 // ----------------------------------------------------------------------------
-// multi-value block reduction: nv doubles per thread -> out[0..nv) in thread v
+// multi-value grid reduction
+//   stage 1 (every block): per-thread sums in R, warp sums in R, the 8 warp
+//     results combined in double, written as partial[(v * nrhs + rhs) * nblk + blk];
+//   stage 2 (last block to arrive): every thread sums a fixed stride of the
+//     blocks for all values, then a block tree in double.  Fixed order: the
+//     result does not depend on block scheduling.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void block_sum_multi(double* vals, int nv, double* sm /* [8][nv] */, int tid) {
+template <class R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R, int NV>
+__device__ __forceinline__ void block_partials(const R* acc, double* sm /* [VB/32][NV] */, double* partial, int nrhs,
+                                               int rhs, unsigned nblk, unsigned blk, int tid) {
   const int lane = tid & 31, w = tid >> 5;
-  for (int v = 0; v < nv; ++v) {
-    double x = warp_sum(vals[v]);
-    if (lane == 0) sm[w * nv + v] = x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R x = warp_sum_r<R>(acc[v]);
+    if (lane == 0) sm[w * NV + v] = (double)x;
   }
   __syncthreads();
-  if (tid < nv) {
+  for (int v = tid; v < NV; v += VB) {
     double t = 0.0;
-    for (int k = 0; k < VB / 32; ++k) t += sm[k * nv + tid];
-    vals[0] = t;  // thread v holds value v
+#pragma unroll
+    for (int k = 0; k < VB / 32; ++k) t += sm[k * NV + v];
+    partial[((size_t)v * nrhs + rhs) * nblk + blk] = t;
+  }
+}
+
+// Stage 2; result for value v in out[v] (shared memory), valid after return.
+template <int NV>
+__device__ __forceinline__ void combine_partials(const double* partial, int nrhs, int rhs, unsigned nblk,
+                                                 double* sm /* [VB/32][NV] */, double* out, int tid) {
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (unsigned b = tid; b < nblk; b += VB) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(partial + ((size_t)v * nrhs + rhs) * nblk + b);
+  }
+  const int lane = tid & 31, w = tid >> 5;
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double x = warp_sum(acc[v]);
+    if (lane == 0) sm[w * NV + v] = x;
+  }
+  __syncthreads();
+  for (int v = tid; v < NV; v += VB) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < VB / 32; ++k) t += sm[k * NV + v];
+    out[v] = t;
   }
   __syncthreads();
 }
@@ -133,22 +181,21 @@ struct CgsArgs {
 
 template <class R, int KN>
 __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* __restrict__ w, CgsArgs a) {
-  constexpr int NVMAX = 2 * KMAX + 1;
-  __shared__ double sm[(VB / 32) * NVMAX];
-  __shared__ double sres[NVMAX];
-  __shared__ R scoef[2 * KMAX];
+  constexpr int NV = 2 * KN + 1;
+  __shared__ double sm[(VB / 32) * NV];
+  __shared__ double sres[NV];
+  __shared__ R scoef[2 * KMAX + 2];
   const int tid = threadIdx.x;
   const int rhs = blockIdx.y;
-  const int kn = KN;
   const long long N = a.n;
-  if (a.update && tid < kn) {
+  if (a.update && tid < KN) {
     scoef[2 * tid] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid];
     scoef[2 * tid + 1] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid + 1];
   }
   __syncthreads();
-  R acc[2 * KN + 1];
+  R acc[NV];
 #pragma unroll
-  for (int v = 0; v < 2 * KN + 1; ++v) acc[v] = 0;
+  for (int v = 0; v < NV; ++v) acc[v] = 0;
   cx<R>* W = w + rhs * N;
   const cx<R>* Vr = V + rhs * N;
   for (long long i = blockIdx.x * (long long)VB + tid; i < N; i += (long long)gridDim.x * VB) {
@@ -168,57 +215,59 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
     }
     if (a.norm) acc[2 * KN] += abs2(wi);
   }
-  const int nv = 2 * KN + 1;
-  double vals[2 * KN + 1];
-#pragma unroll
-  for (int v = 0; v < 2 * KN + 1; ++v) vals[v] = (double)acc[v];
-  block_sum_multi(vals, nv, sm, tid);
   const unsigned nblk = gridDim.x;
-  if (tid < nv) a.red.partial[((size_t)rhs * nblk + blockIdx.x) * nv + tid] = vals[0];
+  block_partials<R, NV>(acc, sm, a.red.partial, a.nrhs, rhs, nblk, blockIdx.x, tid);
   if (!last_block_arrive(a.red.count + rhs, nblk, tid)) return;
-  if (tid < nv) {
-    double t = 0.0;
-    for (unsigned b = 0; b < nblk; ++b) t += __ldcg(a.red.partial + ((size_t)rhs * nblk + b) * nv + tid);
-    sres[tid] = t;
-  }
-  __syncthreads();
+  combine_partials<NV>(a.red.partial, a.nrhs, rhs, nblk, sm, sres, tid);
   if (tid == 0) {
     a.red.count[rhs] = 0;
     double* Hc = a.H ? a.H + ((size_t)rhs * a.hcols + (a.col >= 0 ? a.col : 0)) * a.ld * 2 : nullptr;
+    double* dout = a.dots_out ? a.dots_out + (size_t)rhs * a.ld * 2 : nullptr;
     switch (a.epi) {
       case EPI_STORE:
-        if (a.dots_out)
-          for (int k = 0; k < kn; ++k) {
-            a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
-            a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+        if (dout)
+          for (int k = 0; k < KN; ++k) {
+            dout[2 * k] = sres[2 * k];
+            dout[2 * k + 1] = sres[2 * k + 1];
           }
         if (a.nrm_out) a.nrm_out[rhs] = sres[2 * KN];
         break;
       case EPI_ARNOLDI_FIRST:
-        for (int k = 0; k < kn; ++k) {
+        for (int k = 0; k < KN; ++k) {
           Hc[2 * k] = sres[2 * k];
           Hc[2 * k + 1] = sres[2 * k + 1];
-          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
-          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+          dout[2 * k] = sres[2 * k];
+          dout[2 * k + 1] = sres[2 * k + 1];
         }
         break;
-      case EPI_ARNOLDI_SECOND:
-        for (int k = 0; k < kn; ++k) {
+      case EPI_ARNOLDI_SECOND: {
+        // second Gram-Schmidt pass: add the correction to the column; the norm
+        // of w - V h2 is ||w||^2 - ||h2||^2 for orthonormal V (h2 is tiny)
+        double h2sq = 0.0;
+        for (int k = 0; k < KN; ++k) {
           Hc[2 * k] += sres[2 * k];
           Hc[2 * k + 1] += sres[2 * k + 1];
-          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k] = sres[2 * k];
-          a.dots_out[(size_t)rhs * a.ld * 2 + 2 * k + 1] = sres[2 * k + 1];
+          dout[2 * k] = sres[2 * k];
+          dout[2 * k + 1] = sres[2 * k + 1];
+          h2sq += sres[2 * k] * sres[2 * k] + sres[2 * k + 1] * sres[2 * k + 1];
+        }
+        if (a.norm) {
+          double nrm = sqrt(fmax(sres[2 * KN] - h2sq, 0.0));
+          Hc[2 * KN] = nrm;
+          Hc[2 * KN + 1] = 0.0;
+          // an exactly zero (or denormal) norm ends the Krylov space: the next
+          // basis vector is set to zero and the small solve ignores it
+          if (a.scale_out) a.scale_out[rhs] = (nrm > 1e-300) ? 1.0 / nrm : 0.0;
         }
         break;
+      }
       case EPI_NORMALISE: {
         double nrm = sqrt(sres[2 * KN]);
         if (a.col >= 0) {
-          Hc[2 * kn] = nrm;
-          Hc[2 * kn + 1] = 0.0;
+          Hc[2 * KN] = nrm;
+          Hc[2 * KN + 1] = 0.0;
         }
         if (a.beta_out) a.beta_out[rhs] = nrm;
-        // an exactly zero (or denormal) norm ends the Krylov space: the next
-        // basis vector is set to zero and the small solve ignores it
         if (a.scale_out) a.scale_out[rhs] = (nrm > 1e-300) ? 1.0 / nrm : 0.0;
         break;
       }
@@ -226,9 +275,30 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
   }
 }
 
+// w <- (w - sum_k coef[r][k] V_k) * scale[r]  (third Gram-Schmidt pass fused with
+// the normalisation; no reduction)
+template <class R, int KN>
+__global__ void __launch_bounds__(VB) k_update_scale(const cx<R>* __restrict__ V, cx<R>* __restrict__ w,
+                                                     const double* __restrict__ coef, const double* __restrict__ scale,
+                                                     int n, long long vstride, int ld) {
+  __shared__ R scoef[2 * KMAX + 2];
+  const int rhs = blockIdx.y;
+  if (threadIdx.x < 2 * KN) scoef[threadIdx.x] = (R)coef[(size_t)rhs * ld * 2 + threadIdx.x];
+  __syncthreads();
+  const R sc = (R)scale[rhs];
+  cx<R>* W = w + (long long)rhs * n;
+  const cx<R>* Vr = V + (long long)rhs * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    cx<R> wi = W[i];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) wi -= mkc<R>(scoef[2 * k], scoef[2 * k + 1]) * Vr[k * vstride + i];
+    W[i] = sc * wi;
+  }
+}
+
 template <class R, int KN>
 static void cgs_kn(const KrylovCall& k, const cx<R>* V, cx<R>* w, const CgsArgs& a, cudaStream_t s) {
-  dim3 grid(vec_blocks(k.n), k.nrhs);
+  dim3 grid(red_blocks(k.n), k.nrhs);
   count_launch();
   k_cgs<R, KN><<<grid, VB, 0, s>>>(V, w, a);
 }
@@ -260,6 +330,23 @@ void launch_cgs(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coe
 #define HZ_KN(K) \
   case K: cgs_kn<R, K>(k, V, w, a, s); break;
     HZ_KN(0) HZ_KN(1) HZ_KN(2) HZ_KN(3) HZ_KN(4) HZ_KN(5) HZ_KN(6) HZ_KN(7) HZ_KN(8) HZ_KN(9) HZ_KN(10) HZ_KN(11)
+    HZ_KN(12) HZ_KN(13) HZ_KN(14) HZ_KN(15) HZ_KN(16)
+#undef HZ_KN
+    default: break;
+  }
+}
+
+template <class R>
+void launch_update_scale(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coef, const double* scale,
+                         cudaStream_t s) {
+  dim3 grid(vec_blocks(k.n), k.nrhs);
+  switch (k.kn) {
+#define HZ_KN(K)                                                                               \
+  case K:                                                                                      \
+    count_launch();                                                                            \
+    k_update_scale<R, K><<<grid, VB, 0, s>>>(V, w, coef, scale, k.n, k.vstride, k.ld); \
+    break;
+    HZ_KN(1) HZ_KN(2) HZ_KN(3) HZ_KN(4) HZ_KN(5) HZ_KN(6) HZ_KN(7) HZ_KN(8) HZ_KN(9) HZ_KN(10) HZ_KN(11)
     HZ_KN(12) HZ_KN(13) HZ_KN(14) HZ_KN(15) HZ_KN(16)
 #undef HZ_KN
     default: break;
@@ -381,75 +468,115 @@ void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const doub
 // ----------------------------------------------------------------------------
 // small least squares by complex Givens rotations (one thread per rhs)
 // ----------------------------------------------------------------------------
-struct Cd {
-  double x, y;
-};
-__device__ __forceinline__ Cd cd(double a, double b) { return Cd{a, b}; }
-__device__ __forceinline__ Cd cmulD(Cd a, Cd b) { return cd(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ Cd caddD(Cd a, Cd b) { return cd(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ Cd csubD(Cd a, Cd b) { return cd(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ Cd cconjD(Cd a) { return cd(a.x, -a.y); }
-__device__ __forceinline__ double cabsD(Cd a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ Cd cdivD(Cd a, Cd b) {
-  double d = b.x * b.x + b.y * b.y;
-  return cd((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+// Warp-parallel Givens least squares min || beta e_1 - H y || for one (M+1) x M
+// upper Hessenberg H per right-hand side (one warp each): lane k holds column
+// k in registers; rotation j is formed by lane j and broadcast; the back
+// substitution sums R[i][k] y_k across lanes.  T = float for the complex64
+// hierarchy, double for complex128.
+template <class T, int M>
+__global__ void __launch_bounds__(32) k_lsq_warp(const double* __restrict__ H, const double* __restrict__ beta,
+                                                 double* __restrict__ y, int ld) {
+  const int r = blockIdx.x;
+  const int lane = threadIdx.x;
+  const double* Hr = H + (size_t)r * M * (M + 1) * 2;
+  T cr[M + 1], ci[M + 1];  // column `lane`
+#pragma unroll
+  for (int i = 0; i <= M; ++i) {
+    cr[i] = lane < M ? (T)Hr[(lane * (M + 1) + i) * 2] : (T)0;
+    ci[i] = lane < M ? (T)Hr[(lane * (M + 1) + i) * 2 + 1] : (T)0;
+  }
+  T gr[M + 1], gi[M + 1];
+#pragma unroll
+  for (int i = 0; i <= M; ++i) gr[i] = gi[i] = (T)0;
+  gr[0] = (T)beta[r];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    // lane j forms the rotation that zeroes its subdiagonal entry
+    T c = 1, sr = 0, si = 0;
+    if (lane == j) {
+      const T ar = cr[j], ai = ci[j], br = cr[j + 1], bi = ci[j + 1];
+      const T na = sqrt(ar * ar + ai * ai), nb = sqrt(br * br + bi * bi);
+      const T rr = sqrt(na * na + nb * nb);
+      if (rr == (T)0) {
+        c = 1; sr = 0; si = 0;
+      } else if (na == (T)0) {
+        c = 0; sr = 1; si = 0;
+      } else {
+        c = na / rr;
+        // s = (a / |a|) conj(b) / r
+        const T ur = ar / na, ui = ai / na;
+        sr = (ur * br + ui * bi) / rr;
+        si = (ui * br - ur * bi) / rr;
+      }
+    }
+    c = __shfl_sync(0xffffffffu, c, j);
+    sr = __shfl_sync(0xffffffffu, sr, j);
+    si = __shfl_sync(0xffffffffu, si, j);
+    if (lane >= j && lane < M) {
+      const T t1r = cr[j], t1i = ci[j], t2r = cr[j + 1], t2i = ci[j + 1];
+      // [c s; -conj(s) c] [t1; t2]
+      cr[j] = c * t1r + (sr * t2r - si * t2i);
+      ci[j] = c * t1i + (sr * t2i + si * t2r);
+      cr[j + 1] = c * t2r - (sr * t1r + si * t1i);
+      ci[j + 1] = c * t2i - (sr * t1i - si * t1r);
+    }
+    const T g1r = gr[j], g1i = gi[j], g2r = gr[j + 1], g2i = gi[j + 1];
+    gr[j] = c * g1r + (sr * g2r - si * g2i);
+    gi[j] = c * g1i + (sr * g2i + si * g2r);
+    gr[j + 1] = c * g2r - (sr * g1r + si * g1i);
+    gi[j + 1] = c * g2i - (sr * g1i - si * g1r);
+  }
+  // back substitution: y_i = (g_i - sum_{k>i} R[i][k] y_k) / R[i][i]
+  T yr = 0, yi = 0;  // y_lane
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i) {
+    T pr = 0, pi = 0;
+    if (lane > i && lane < M) {
+      pr = cr[i] * yr - ci[i] * yi;
+      pi = cr[i] * yi + ci[i] * yr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pr += __shfl_xor_sync(0xffffffffu, pr, o);
+      pi += __shfl_xor_sync(0xffffffffu, pi, o);
+    }
+    if (lane == i) {
+      const T tr = gr[i] - pr, ti = gi[i] - pi;
+      const T dr = cr[i], di = ci[i];
+      const T d2 = dr * dr + di * di;
+      if (d2 > (T)0) {
+        yr = (tr * dr + ti * di) / d2;
+        yi = (ti * dr - tr * di) / d2;
+      } else {
+        yr = yi = 0;
+      }
+    }
+  }
+  if (lane < M) {
+    y[((size_t)r * ld + lane) * 2] = (double)yr;
+    y[((size_t)r * ld + lane) * 2 + 1] = (double)yi;
+  }
 }
 
-// Solve min || beta e_1 - H y || for H (m+1) x m upper Hessenberg (column-major,
-// leading dim ldh, entries (re, im)); y (m entries) written to yout.
-__device__ void givens_lsq(const double* H, int ldh, int m, double beta, double* yout) {
-  Cd R[KMAX + 1][KMAX];
-  Cd g[KMAX + 1];
-  for (int j = 0; j < m; ++j)
-    for (int i = 0; i <= m; ++i) R[i][j] = cd(H[(j * ldh + i) * 2], H[(j * ldh + i) * 2 + 1]);
-  for (int i = 0; i <= m; ++i) g[i] = cd(0, 0);
-  g[0] = cd(beta, 0);
-  for (int j = 0; j < m; ++j) {
-    Cd a = R[j][j], b = R[j + 1][j];
-    double na = cabsD(a), nb = cabsD(b);
-    double r = hypot(na, nb);
-    double c;
-    Cd s;
-    if (r == 0.0) {
-      c = 1.0;
-      s = cd(0, 0);
-    } else if (na == 0.0) {
-      c = 0.0;
-      s = cd(1, 0);
-    } else {
-      c = na / r;
-      Cd ua = cd(a.x / na, a.y / na);
-      s = cmulD(ua, cd(b.x / r, -b.y / r));
-    }
-    for (int k = j; k < m; ++k) {
-      Cd t1 = R[j][k], t2 = R[j + 1][k];
-      R[j][k] = caddD(cd(c * t1.x, c * t1.y), cmulD(s, t2));
-      R[j + 1][k] = csubD(cd(c * t2.x, c * t2.y), cmulD(cconjD(s), t1));
-    }
-    Cd g1 = g[j], g2 = g[j + 1];
-    g[j] = caddD(cd(c * g1.x, c * g1.y), cmulD(s, g2));
-    g[j + 1] = csubD(cd(c * g2.x, c * g2.y), cmulD(cconjD(s), g1));
-  }
-  Cd y[KMAX];
-  for (int i = m - 1; i >= 0; --i) {
-    Cd t = g[i];
-    for (int k = i + 1; k < m; ++k) t = csubD(t, cmulD(R[i][k], y[k]));
-    y[i] = (cabsD(R[i][i]) > 0.0) ? cdivD(t, R[i][i]) : cd(0, 0);
-  }
-  for (int i = 0; i < m; ++i) {
-    yout[2 * i] = y[i].x;
-    yout[2 * i + 1] = y[i].y;
+template <class T>
+static void lsq_t(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s) {
+  switch (m) {
+#define HZ_M(MM)                                                   \
+  case MM:                                                         \
+    count_launch();                                                \
+    k_lsq_warp<T, MM><<<nrhs, 32, 0, s>>>(H, beta, y, ld); \
+    break;
+    HZ_M(1) HZ_M(2) HZ_M(3) HZ_M(4) HZ_M(5) HZ_M(6) HZ_M(7) HZ_M(8) HZ_M(9) HZ_M(10) HZ_M(11) HZ_M(12) HZ_M(13)
+    HZ_M(14) HZ_M(15) HZ_M(16)
+#undef HZ_M
+    default: break;
   }
 }
 
-__global__ void k_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  givens_lsq(H + (size_t)r * m * (m + 1) * 2, m + 1, m, beta[r], y + (size_t)r * ld * 2);
-}
-void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s) {
-  count_launch();
-  k_lsq<<<(nrhs + 31) / 32, 32, 0, s>>>(H, beta, y, m, ld, nrhs);
+void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, int nrhs, cudaStream_t s,
+                bool single) {
+  if (single) lsq_t<float>(H, beta, y, m, ld, nrhs, s);
+  else lsq_t<double>(H, beta, y, m, ld, nrhs, s);
 }
 
 // ----------------------------------------------------------------------------
@@ -460,9 +587,10 @@ __global__ void __launch_bounds__(VB) k_gram(const cx<R>* __restrict__ P, long l
                                              Reduce red) {
   constexpr int NG = KN * (KN + 1) / 2;
   constexpr int NV = 2 * NG;
+  constexpr int S = KN - 1;
   __shared__ double sm[(VB / 32) * NV];
   __shared__ double sres[NV];
-  const int tid = threadIdx.x, rhs = blockIdx.y;
+  const int tid = threadIdx.x, rhs = blockIdx.y, nrhs = gridDim.y;
   R acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0;
@@ -482,70 +610,96 @@ __global__ void __launch_bounds__(VB) k_gram(const cx<R>* __restrict__ P, long l
         ++q;
       }
   }
-  double vals[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) vals[v] = (double)acc[v];
-  block_sum_multi(vals, NV, sm, tid);
   const unsigned nblk = gridDim.x;
-  if (tid < NV) red.partial[((size_t)rhs * nblk + blockIdx.x) * NV + tid] = vals[0];
+  block_partials<R, NV>(acc, sm, red.partial, nrhs, rhs, nblk, blockIdx.x, tid);
   if (!last_block_arrive(red.count + rhs, nblk, tid)) return;
-  if (tid < NV) {
-    double t = 0.0;
-    for (unsigned b = 0; b < nblk; ++b) t += __ldcg(red.partial + ((size_t)rhs * nblk + b) * NV + tid);
-    sres[tid] = t;
-  }
-  __syncthreads();
+  combine_partials<NV>(red.partial, nrhs, rhs, nblk, sm, sres, tid);
   if (tid != 0) return;
   red.count[rhs] = 0;
-  // Hermitian Gram G[a][b] = <p_a, p_b>
-  Cd G[KN][KN];
-  int q = 0;
-  for (int a = 0; a < KN; ++a)
-    for (int b = a; b < KN; ++b) {
-      G[a][b] = cd(sres[2 * q], sres[2 * q + 1]);
-      G[b][a] = cconjD(G[a][b]);
-      ++q;
-    }
-  // Cholesky G = U^H U (U upper triangular); a pivot that is not clearly
-  // positive ends the basis there (the remaining directions are dropped).
-  Cd U[KN][KN];
-  for (int a = 0; a < KN; ++a)
-    for (int b = 0; b < KN; ++b) U[a][b] = cd(0, 0);
-  const double g00 = G[0][0].x;
-  int rank = KN;
-  for (int j = 0; j < KN; ++j) {
-    double d = G[j][j].x;
-    for (int k = 0; k < j; ++k) d -= U[k][j].x * U[k][j].x + U[k][j].y * U[k][j].y;
-    if (!(d > 1e-13 * g00) || !(g00 > 0.0)) {
-      rank = j;
-      break;
-    }
-    double ujj = sqrt(d);
-    U[j][j] = cd(ujj, 0);
-    for (int b = j + 1; b < KN; ++b) {
-      Cd t = G[j][b];
-      for (int k = 0; k < j; ++k) t = csubD(t, cmulD(cconjD(U[k][j]), U[k][b]));
-      U[j][b] = cd(t.x / ujj, t.y / ujj);
+  // Gram entries G[a][b] = <p_a, p_b>, a <= b, in the order accumulated above
+  auto gidx = [](int a, int b) { return a * KN - a * (a - 1) / 2 + (b - a); };
+  // normal equations of min || p_0 - sum_k y_k p_{k+1} ||:  G_rr y = g_r0 with
+  // G_rr = [<p_a, p_b>]_{a,b>=1}, g_r0 = [<p_a, p_0>]_{a>=1}; Cholesky G_rr = U^H U
+  double Ur[S][S], Ui[S][S];
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int b = 0; b < S; ++b) Ur[a][b] = Ui[a][b] = 0.0;
+  double dmax = 0.0;
+#pragma unroll
+  for (int a = 1; a < KN; ++a) dmax = fmax(dmax, sres[2 * gidx(a, a)]);
+  int rank = S;
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    if (j < rank) {
+      double d = sres[2 * gidx(j + 1, j + 1)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d -= Ur[k][j] * Ur[k][j] + Ui[k][j] * Ui[k][j];
+      if (!(d > 1e-13 * dmax)) {
+        rank = j;  // drop the remaining (numerically dependent) directions
+      } else {
+        const double ujj = sqrt(d), inv = 1.0 / ujj;
+        Ur[j][j] = ujj;
+#pragma unroll
+        for (int b = j + 1; b < S; ++b) {
+          double tr = sres[2 * gidx(j + 1, b + 1)], ti = sres[2 * gidx(j + 1, b + 1) + 1];
+#pragma unroll
+          for (int k = 0; k < j; ++k) {  // t -= conj(U[k][j]) U[k][b]
+            tr -= Ur[k][j] * Ur[k][b] + Ui[k][j] * Ui[k][b];
+            ti -= Ur[k][j] * Ui[k][b] - Ui[k][j] * Ur[k][b];
+          }
+          Ur[j][b] = tr * inv;
+          Ui[j][b] = ti * inv;
+        }
+      }
     }
   }
-  // min || U e_0 - U[:, 1:] y ||, U[:,1:] is upper Hessenberg with first column
-  // (U01, U11, 0 ...); rhs U e_0 = U00 e_0.
-  const int m = KN - 1;
-  double Hs[(KMAX + 1) * KMAX * 2];
-  for (int j = 0; j < m; ++j)
-    for (int i = 0; i <= m; ++i) {
-      Cd v = (j + 1 < rank && i <= j + 1) ? U[i][j + 1] : cd(0, 0);
-      Hs[(j * (m + 1) + i) * 2] = v.x;
-      Hs[(j * (m + 1) + i) * 2 + 1] = v.y;
+  // U^H z = g_r0 (forward), then U y = z (backward); g_r0[a] = <p_{a+1}, p_0> = conj(G[0][a+1])
+  double zr[S], zi[S], yr[S], yi[S];
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    zr[a] = zi[a] = yr[a] = yi[a] = 0.0;
+  }
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    if (a < rank) {
+      double tr = sres[2 * gidx(0, a + 1)], ti = -sres[2 * gidx(0, a + 1) + 1];
+#pragma unroll
+      for (int k = 0; k < a; ++k) {  // t -= conj(U[k][a]) z_k
+        tr -= Ur[k][a] * zr[k] + Ui[k][a] * zi[k];
+        ti -= Ur[k][a] * zi[k] - Ui[k][a] * zr[k];
+      }
+      zr[a] = tr / Ur[a][a];
+      zi[a] = ti / Ur[a][a];
     }
-  double beta = rank > 0 ? U[0][0].x : 0.0;
-  givens_lsq(Hs, m + 1, m, beta, y + (size_t)rhs * ld * 2);
+  }
+#pragma unroll
+  for (int a = S - 1; a >= 0; --a) {
+    if (a < rank) {
+      double tr = zr[a], ti = zi[a];
+#pragma unroll
+      for (int k = a + 1; k < S; ++k) {
+        if (k < rank) {
+          tr -= Ur[a][k] * yr[k] - Ui[a][k] * yi[k];
+          ti -= Ur[a][k] * yi[k] + Ui[a][k] * yr[k];
+        }
+      }
+      yr[a] = tr / Ur[a][a];
+      yi[a] = ti / Ur[a][a];
+    }
+  }
+  double* yo = y + (size_t)rhs * ld * 2;
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    yo[2 * a] = yr[a];
+    yo[2 * a + 1] = yi[a];
+  }
 }
 
 template <class R>
 void launch_gram_lsq(const cx<R>* P, long long pstride, int kn, int n, int nrhs, double* y, int ld,
                      const Reduce& red, cudaStream_t s) {
-  dim3 grid(vec_blocks(n), nrhs);
+  dim3 grid(red_blocks(n), nrhs);
   switch (kn) {
     case 2: count_launch();
       k_gram<R, 2><<<grid, VB, 0, s>>>(P, pstride, n, y, ld, red); break;
@@ -642,6 +796,8 @@ void launch_scatter(const cx<double>* vals, const int* rec, int nrec, int n, int
   template void launch_cgs<R>(const KrylovCall&, const cx<R>*, cx<R>*, const double*, bool, bool, bool, double*,   \
                               double*, int, double*, int, double*, double*, const Reduce&, cudaStream_t);          \
   template void launch_norm2<R>(const cx<R>*, int, int, const Reduce&, cudaStream_t);                              \
+  template void launch_update_scale<R>(const KrylovCall&, const cx<R>*, cx<R>*, const double*, const double*,       \
+                                       cudaStream_t);                              \
   template void launch_scale<R>(const cx<R>*, cx<R>*, const double*, int, int, cudaStream_t);                      \
   template void launch_combine<R>(const cx<R>*, long long, int, const double*, int, const cx<R>*, cx<R>*, int, int, \
                                   cudaStream_t);                                                                   \

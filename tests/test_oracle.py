@@ -173,6 +173,23 @@ def test_matrix_free_equals_kronecker_assembly(L, sigma):
     assert np.allclose(iofd.operator_Q(prob)(xq).ravel(), MQ @ xq.ravel(), atol=1e-13)
 
 
+def test_pointwise_rows_equal_full_grid_rows():
+    """The sampled-row evaluator (used for checks at full sizes) gives the same
+    rows as the full-grid evaluator, inside and outside the PML."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    rng = np.random.default_rng(8)
+    for L, sig in [(0, 0.0), (1, 0.9)]:
+        lev = prob.levels[L]
+        pts = [rng.integers(0, m, 40) for m in lev.shape]
+        for d in iofd.OFFSETS[::5]:
+            full = iofd.row_coefficient(lev, prob.tables, d, sig)[pts[0], pts[1], pts[2]]
+            part = iofd.row_coefficient_points(lev, prob.tables, d, *pts, shift_sigma=sig)
+            assert np.allclose(full, part, rtol=1e-14, atol=0)
+            lazy = iofd.make_level_points(w.c, w.n_pml, w.h, w.omega, w.gamma_max, L)
+            part2 = iofd.row_coefficient_points(lazy, prob.tables, d, *pts, shift_sigma=sig)
+            assert np.allclose(full, part2, rtol=1e-14, atol=0)
+
+
 def test_pml_without_stretch_equals_interior_form():
     """gamma_max = 0 removes every PML term: the stencil is the shell form everywhere."""
     w, prob0 = small_problem(n=16, n_pml=4, gamma_max=0.0)
