@@ -146,6 +146,26 @@ hz_status iofd_coeffs(hz_handle* h, int level, double* kappa_dev, double* shell_
 hz_status iofd_apply(hz_handle* h, int level, int op, int precision, const void* x_dev, void* y_dev, int nrhs,
                      void* stream);
 
+/* r = g - Op x and norm2[k] = ||r_k||^2 for each right-hand side k, without
+ * allocating device memory during the call.  The paper has no counterpart:
+ * this serves callers that cannot allocate at call time (stream capture with
+ * allocation forbidden, fixed-budget real-time loops, embedding hosts).  The
+ * norm's grid-wide reduction keeps its per-block partial sums and arrival
+ * counters in a file-scope device array of the library (512 KiB of partial
+ * sums + 64 counters, held on every device that loads the library until the
+ * process exits) instead of the handle's workspace.
+ *   op             HZ_OP_A, HZ_OP_B, HZ_OP_A_ADJ or HZ_OP_B_ADJ.
+ *   g_dev, x_dev   DEVICE inputs, r_dev DEVICE output (N_L * nrhs, `precision`);
+ *                  r must not alias g or x.
+ *   norm2_dev      DEVICE double, nrhs values out.
+ * Limits: nrhs <= 64 and (stencil blocks per rhs) * nrhs <= 65536; larger
+ * problems return HZ_EINVAL with a message.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and should come before
+ * any stream capture.  Every call shares the one array: calls that overlap on
+ * the GPU (concurrent streams, several handles) race and must be serialised. */
+hz_status iofd_residual_static(hz_handle* h, int level, int op, int precision, const void* g_dev, const void* x_dev,
+                               void* r_dev, double* norm2_dev, int nrhs, void* stream);
+
 /* z = M_h^{-1} r: one application of the three-grid preconditioner of
  * Algorithm 1 (pre-smooth S_h(r;0), restrict r - A_h z_pre, K_2h, prolong and
  * correct, post-smooth S_h(r; z~)), with the shifted 2h-4h cycle of

@@ -24,7 +24,7 @@ _STATUS = {0: "HZ_OK", 1: "HZ_EINVAL", 2: "HZ_ENOMEM", 3: "HZ_ECUDA", 4: "HZ_ENO
 
 EXPORTED = ["hz_default_params", "hz_create", "hz_destroy", "hz_last_error", "hz_workspace_bytes",
             "hz_set_params", "iofd_coeffs", "iofd_apply", "threegrid_precond", "helmholtz_solve",
-            "helmholtz_adjoint_grad", "hz_kernel_launches"]
+            "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static"]
 
 
 class HzGrid(ctypes.Structure):
@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hz_kernel_launches.restype = ctypes.c_ulonglong
     lib.iofd_coeffs.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.iofd_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
+    lib.iofd_residual_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
+                                         ctypes.c_int, vp]
     lib.threegrid_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
     lib.helmholtz_solve.argtypes = [vp, P(HzSource), ctypes.c_int, vp, vp, P(HzStats)]
     lib.helmholtz_adjoint_grad.argtypes = [vp, P(HzSource), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
@@ -193,6 +195,24 @@ class Solver:
         self._ok(self._lib.iofd_apply(self._h, level, op, prec, ctypes.c_void_p(x.data_ptr()),
                                       ctypes.c_void_p(y.data_ptr()), nrhs, _stream_ptr(stream)))
         return y
+
+    # -- iofd_residual_static --------------------------------------------------
+    def residual_static(self, g, x, op=HZ_OP_A, level=0, out=None, norm2_out=None, stream=None):
+        """r = g - Op x and ||r||^2 per right-hand side through the entry point
+        that allocates no device memory (its reduction scratch is a static
+        device array of the library); returns (r, norm2)."""
+        import torch
+        prec = HZ_C64 if x.dtype == torch.complex64 else HZ_C128
+        n = self.N[level]
+        nrhs = x.numel() // n
+        _check_field(x, x.dtype, n * nrhs, "x")
+        _check_field(g, x.dtype, n * nrhs, "g")
+        r = torch.empty_like(x) if out is None else out
+        n2 = torch.empty(nrhs, dtype=torch.float64, device="cuda") if norm2_out is None else norm2_out
+        self._ok(self._lib.iofd_residual_static(self._h, level, op, prec, ctypes.c_void_p(g.data_ptr()),
+                                                ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                                ctypes.c_void_p(n2.data_ptr()), nrhs, _stream_ptr(stream)))
+        return r, n2
 
     # -- threegrid_precond ---------------------------------------------------
     def threegrid_precond(self, r, adjoint=False, out=None, stream=None):

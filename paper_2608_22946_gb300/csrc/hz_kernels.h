@@ -45,6 +45,7 @@ struct StencilCall {
 
 template <class R>
 void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s);
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs);
 
 // Grid transfers (Eq. full-weighting, Eq. linear-prolongation).
 template <class R>

@@ -1212,3 +1212,85 @@ hz_status helmholtz_adjoint_grad(hz_handle* H, const hz_source* src, int nsrc, c
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free residual: r = g - Op x and ||r||^2 per right-hand side.
+//
+// For callers that cannot allocate device memory at call time: code running
+// while a CUDA graph is being captured with allocation forbidden, real-time
+// loops whose memory budget is fixed up front, or hosts embedding the solver
+// inside an allocator they do not control.  The grid-wide reduction of the
+// residual norm needs scratch (one partial sum per block and per right-hand
+// side, plus an arrival counter per right-hand side); here it lives in the
+// file-scope device array below instead of the handle's workspace, so the
+// call itself never allocates.  The handle must already exist.
+// ============================================================================
+namespace {
+
+constexpr long long kResidStaticPartials = 1 << 16;  // doubles (512 KiB)
+constexpr int kResidStaticMaxRhs = 64;
+// [partials (kResidStaticPartials) | norm2 staging (64) | counters (64, as unsigned)]
+static __device__ __align__(256) double g_resid_static[kResidStaticPartials + 2 * kResidStaticMaxRhs];
+
+constexpr int kMaxDevices = 64;
+double* g_resid_static_addr[kMaxDevices] = {};
+
+// Host-side stand-in -> device address, once per device (with that device current).
+double* resid_static_scratch() {
+  int dev = 0;
+  HZ_CK(cudaGetDevice(&dev));
+  HZ_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal out of range");
+  if (!g_resid_static_addr[dev]) {
+    void* p = nullptr;
+    HZ_CK(cudaGetSymbolAddress(&p, g_resid_static));
+    g_resid_static_addr[dev] = (double*)p;
+  }
+  return g_resid_static_addr[dev];
+}
+
+}  // namespace
+
+extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int precision, const void* g,
+                                          const void* x, void* r, double* norm2, int nrhs, void* stream) {
+  if (!H) return HZ_EINVAL;
+  return run_guarded(H, [&] {
+    HZ_REQUIRE(level >= 0 && level <= 2, "level must be 0, 1 or 2");
+    HZ_REQUIRE(op == HZ_OP_A || op == HZ_OP_B || op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ,
+               "operator must be A, B or their adjoints");
+    HZ_REQUIRE(g && x && r && norm2 && r != x && r != g, "g, x, r, norm2 must be non-null and r distinct");
+    HZ_REQUIRE(precision == HZ_C64 || precision == HZ_C128, "precision must be HZ_C64 or HZ_C128");
+    HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
+    HZ_REQUIRE(nrhs <= kResidStaticMaxRhs, "nrhs exceeds the static scratch limit of 64 right-hand sides");
+    const Level& lv = H->lev[level];
+    const long long need = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs) * nrhs;
+    HZ_REQUIRE(need <= kResidStaticPartials,
+               "grid too large for the static scratch (" + std::to_string(need) + " block partial sums > " +
+                   std::to_string(kResidStaticPartials) + ")");
+    double* base = resid_static_scratch();
+    cudaStream_t st = (cudaStream_t)stream;
+    Reduce red;
+    red.partial = base;
+    red.out = norm2;
+    red.count = reinterpret_cast<unsigned*>(base + kResidStaticPartials + kResidStaticMaxRhs);
+    // the arrival counters must start at zero (the last block also resets them)
+    HZ_CK(cudaMemsetAsync(red.count, 0, sizeof(unsigned) * nrhs, st));
+    const bool adj = (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ);
+    const bool shifted = (op == HZ_OP_B || op == HZ_OP_B_ADJ);
+    if (precision == HZ_C64) {
+      StencilCall<float> c = call<float>(H, level, shifted, nrhs);
+      c.x = (const cx<float>*)x;
+      c.g = (const cx<float>*)g;
+      c.y = (cx<float>*)r;
+      c.red = red;
+      launch_stencil<float>(c, M_RESID, OP_AB, adj, st);
+    } else {
+      StencilCall<double> c = call<double>(H, level, shifted, nrhs);
+      c.x = (const cx<double>*)x;
+      c.g = (const cx<double>*)g;
+      c.y = (cx<double>*)r;
+      c.red = red;
+      launch_stencil<double>(c, M_RESID, OP_AB, adj, st);
+    }
+    HZ_LAUNCHED();
+  });
+}

@@ -786,6 +786,13 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
   }
 }
 
+// Blocks per right-hand side of a forward stencil launch on this grid (the
+// size of the per-block partial-sum array its reductions need).
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs) {
+  int zb = choose_zblock(nx, ny, nz, nrhs);
+  return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zb - 1) / zb);
+}
+
 template <class R, int MODE, int OP>
 static void set_adj_attr() {
   constexpr int NP = AdjNP<OP>::v;
