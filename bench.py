@@ -209,6 +209,11 @@ def run_gpu(args):
         sources = w.sources[:1]
         nrhs = 1
     params = hz.default_params(tol=1e-6, precision=hz.HZ_C64)
+    noconv = False
+    if args.max_pc:
+        # profiling runs: cap the preconditioner calls (same kernel mix, bounded length)
+        params.max_pc = args.max_pc
+        noconv = True
     c_host = torch.from_numpy(w.c.reshape(-1)).pin_memory()
     c_dev = c_host.to("cuda", non_blocking=True)
     log(f"workload {w.name} n={w.n} ready")
@@ -217,7 +222,7 @@ def run_gpu(args):
     v = torch.empty((nrhs,) + s.shape, dtype=torch.complex128, device="cuda")
     u = torch.empty_like(v)
     for it in range(args.warmup):
-        _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u)
+        _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u, allow_noconv=noconv)
         log(f"warmup {it}: pc={st['pc_calls']} passes={st['refine_passes']} rel={st['rel_res']:.2e} "
             f"t={st['t_solve']:.3f}s")
     torch.cuda.synchronize()
@@ -231,7 +236,7 @@ def run_gpu(args):
     with ClockSampler(dev) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u)
+            _, _, st = s.helmholtz_solve(sources, v_out=v, u_out=u, allow_noconv=noconv)
             stats.append(st)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -382,6 +387,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--stencil-only", action="store_true")
+    ap.add_argument("--max-pc", type=int, default=0, help="profiling only: cap preconditioner calls")
     args = ap.parse_args()
     if args.stencil_only:
         run_stencil_only(args)

@@ -32,13 +32,22 @@ template <class R> __host__ __device__ __forceinline__ cx<R> conjc(cx<R> a) { re
 template <class R> __host__ __device__ __forceinline__ cx<R> cjmul(cx<R> a, cx<R> b) {
   return mkc<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// 1/d: a correctly rounded reciprocal instead of an IEEE division in single precision
+__host__ __device__ __forceinline__ float recip(float d) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(d);
+#else
+  return 1.0f / d;
+#endif
+}
+__host__ __device__ __forceinline__ double recip(double d) { return 1.0 / d; }
 template <class R> __host__ __device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) {
-  R d = b.x * b.x + b.y * b.y;
-  return mkc<R>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+  const R r = recip(b.x * b.x + b.y * b.y);
+  return mkc<R>((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
 }
 template <class R> __host__ __device__ __forceinline__ cx<R> cinv(cx<R> b) {
-  R d = b.x * b.x + b.y * b.y;
-  return mkc<R>(b.x / d, -b.y / d);
+  const R r = recip(b.x * b.x + b.y * b.y);
+  return mkc<R>(b.x * r, -b.y * r);
 }
 template <class R> __host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.x * a.x + a.y * a.y; }
 template <class R, class S> __host__ __device__ __forceinline__ cx<R> cvt(cx<S> a) { return mkc<R>((R)a.x, (R)a.y); }

@@ -27,6 +27,7 @@
 // it needs the neighbours' own coefficients, which it evaluates once per
 // loaded node into shared memory.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 
 #include "hz_kernels.h"
@@ -218,10 +219,12 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   const int nplanes = zb1 - zb0 + 2;
   const long long N = L.N;
   const cx<R>* X = a.x + rhs * N;
+  cx<R>* Y = a.y + rhs * N;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = (gx < L.nx) && (gy < L.ny);
-  const long long col = (long long)gy * L.nx + gx;
-  const long long plane_sz = (long long)L.nx * L.ny;
+  // fields have fewer than 2^31 nodes (checked at creation): 32-bit offsets
+  const int col = gy * L.nx + gx;
+  const int plane_sz = L.nx * L.ny;
   const R inv_ell2 = L.inv_ell2;
   const cx<R> shift = a.mass_shift;
   const int nseg = a.tab.nseg;
@@ -240,32 +243,40 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
 
   // this thread's (at most two) load slots in every plane, fixed for the march
   const bool has1 = tid + NT < PLANE;
-  int li0 = tid, li1 = tid + NT;
-  long long go0 = 0, go1 = 0;
+  const int li0 = tid, li1 = tid + NT;
+  int go0 = 0, go1 = 0;
   bool in0, in1 = false;
   {
     int ly = li0 / PW, lx = li0 - ly * PW;
     int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
     in0 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
-    go0 = in0 ? (long long)qy * L.nx + qx : 0;
+    go0 = in0 ? qy * L.nx + qx : 0;
     if (has1) {
       ly = li1 / PW;
       lx = li1 - ly * PW;
       qx = x0 - 1 + lx;
       qy = y0 - 1 + ly;
       in1 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
-      go1 = in1 ? (long long)qy * L.nx + qx : 0;
+      go1 = in1 ? qy * L.nx + qx : 0;
     }
   }
+  // shared-memory addresses of this thread's load slots in stage 0
+  const unsigned sx0 = (unsigned)__cvta_generic_to_shared(&sX[0][li0]);
+  const unsigned sx1 = (unsigned)__cvta_generic_to_shared(&sX[0][li1]);
+  constexpr unsigned kStageBytes = PLANE * sizeof(cx<R>);
   auto issue = [&](int z, int st) {
-    const bool zin = (z >= 0) && (z < L.nz);
-    const long long zo = zin ? (long long)z * plane_sz : 0;
+    const bool zin = (unsigned)z < (unsigned)L.nz;
+    const int zo = zin ? z * plane_sz : 0;
     const bool p0 = zin && in0, p1 = zin && in1;
-    cp_async<sizeof(cx<R>)>(&sX[st][li0], X + (p0 ? zo + go0 : 0), p0);
-    if (has1) cp_async<sizeof(cx<R>)>(&sX[st][li1], X + (p1 ? zo + go1 : 0), p1);
+    const unsigned so = (unsigned)st * kStageBytes;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sx0 + so), "l"(X + (zo + go0)),
+                 "n"(sizeof(cx<R>)), "r"(p0 ? (int)sizeof(cx<R>) : 0));
+    if (has1)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sx1 + so), "l"(X + (zo + go1)),
+                   "n"(sizeof(cx<R>)), "r"(p1 ? (int)sizeof(cx<R>) : 0));
     if (MODE == M_J2) {
-      cp_async<sizeof(R)>(&sK[st][li0], L.kappa + (p0 ? zo + go0 : 0), p0);
-      if (has1) cp_async<sizeof(R)>(&sK[st][li1], L.kappa + (p1 ? zo + go1 : 0), p1);
+      cp_async<sizeof(R)>(&sK[st][li0], L.kappa + (zo + go0), p0);
+      if (has1) cp_async<sizeof(R)>(&sK[st][li1], L.kappa + (zo + go1), p1);
     }
     cp_commit();
   };
@@ -277,28 +288,34 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
     else cp_commit();
   }
 
-  Part<R, GEN> wm, w0, wp;
-  zero_part(wm);
-  zero_part(w0);
-  R kap_prev = 0, kap_cur = 0;
-  cx<R> g_prev = mkc<R>(0, 0), g_cur = mkc<R>(0, 0);      // RESID/JSWEEP rhs, J2 raw g
-  cx<R> xc_prev = mkc<R>(0, 0), xc_cur = mkc<R>(0, 0);    // JSWEEP iterate / J2 y1 at centre
-  cx<R> dinv_prev = mkc<R>(0, 0), dinv_cur = mkc<R>(0, 0);
+  // Three planes of partial sums and two planes of per-row values live in
+  // registers; the z-march is unrolled by NSTAGE so that the ring stage, the
+  // window slot and the previous/current slot of every step are compile-time
+  // constants (no register moves, no modulo).
+  Part<R, GEN> w[3];
+  zero_part(w[0]);
+  zero_part(w[1]);
+  zero_part(w[2]);
+  R kapv[2] = {0, 0};
+  cx<R> gv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};      // RESID/JSWEEP rhs, J2 raw g
+  cx<R> xcv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};     // JSWEEP iterate / J2 y1 at the centre
+  cx<R> dinvv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};
   double nrm2 = 0.0;
   const cx<R>* G = (MODE == M_RESID || MODE == M_JSWEEP) ? a.g + rhs * N : nullptr;
+  const cx<R>* Bs = a.base ? a.base + rhs * N : nullptr;
 
-  for (int k = 0; k < nplanes; ++k) {
+  auto step = [&](auto Sc, int k) {
+    constexpr int S = decltype(Sc)::value;    // k % NSTAGE
+    constexpr int CUR = S % 3, PRV = (S + 2) % 3, PP = (S + 1) % 3;
+    constexpr int C2 = S % 2, P2 = (S + 1) % 2;
     const int zk = zb0 - 1 + k;
-    const int st = k % NSTAGE;
     cp_wait<PREF - 1>();
     __syncthreads();
-    {
-      const int kk = k + PREF;
-      if (kk < nplanes) issue(zb0 - 1 + kk, kk % NSTAGE);
-      else cp_commit();
-    }
-    const bool zin = (zk >= 0) && (zk < L.nz);
-    const cx<R>* P = sX[st];
+    // plane k + PREF goes to the stage plane k - 1 used (PREF = NSTAGE - 1)
+    if (k + PREF < nplanes) issue(zk + PREF, (S + PREF) % NSTAGE);
+    else cp_commit();
+    const bool zin = (unsigned)zk < (unsigned)L.nz;
+    const cx<R>* P = sX[S];
     if (MODE == M_J2) {
       // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first sweep)
       const cx<R> abz = zin ? L.abar[2][zk] : mkc<R>(1, 0);
@@ -320,7 +337,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         const bool in = zin && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
         cx<R> y1 = mkc<R>(0, 0), dinv = mkc<R>(0, 0);
         const cx<R> g = P[li];
-        const R kap = sK[st][li];
+        const R kap = sK[S][li];
         if (in) {
           R a1, a4;
           table_a1a4<R>(sTab, nseg, ds, inv_ds, eta_star(kap), a1, a4);
@@ -331,27 +348,31 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         }
         sY1[li] = y1;
         if (e < NT) {
-          g_cur = g;
-          kap_cur = kap;
-          dinv_cur = dinv;
-          xc_cur = y1;
+          gv[C2] = g;
+          kapv[C2] = kap;
+          dinvv[C2] = dinv;
+          xcv[C2] = y1;
         }
       }
       __syncthreads();
       P = sY1;
     } else {
       if (active && zin) {
-        const long long idx = (long long)zk * plane_sz + col;
-        kap_cur = L.kappa[idx];
-        if (MODE == M_RESID || MODE == M_JSWEEP) g_cur = G[idx];
-        if (MODE == M_JSWEEP) xc_cur = P[(ty + 1) * PW + tx + 1];
+        const int idx = zk * plane_sz + col;
+        kapv[C2] = L.kappa[idx];
+        if (MODE == M_RESID || MODE == M_JSWEEP) gv[C2] = G[idx];
+        if (MODE == M_JSWEEP) xcv[C2] = P[(ty + 1) * PW + tx + 1];
       }
     }
-    partials(P, tx + 1, ty + 1, wp);
+    partials(P, tx + 1, ty + 1, w[CUR]);
 
     if (k >= 2 && active) {
+      const Part<R, GEN>& wm = w[PP];
+      const Part<R, GEN>& w0 = w[PRV];
+      const Part<R, GEN>& wp = w[CUR];
+      const R kap_prev = kapv[P2];
       const int z = zk - 1;
-      const long long idx = (long long)z * plane_sz + col;
+      const int idx = z * plane_sz + col;
       cx<R> out;
       if constexpr (OP == OP_Q) {
         R bv[3];
@@ -392,24 +413,28 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         if (MODE == M_APPLY) {
           out = Hx;
         } else if (MODE == M_RESID) {
-          out = g_prev - Hx;
+          out = gv[P2] - Hx;
         } else if (MODE == M_J2) {
-          out = xc_prev + a.omega_j * (dinv_prev * (g_prev - Hx));
-          if (a.base) out += a.base[rhs * N + idx];
+          out = xcv[P2] + a.omega_j * (dinvv[P2] * (gv[P2] - Hx));
+          if (Bs) out += Bs[idx];
         } else {  // M_JSWEEP
           const cx<R> D = inv_ell2 * ((R)2 * av[3] * sab) - (mk * av[0]) * shift;
-          out = xc_prev + a.omega_j * cdiv(g_prev - Hx, D);
+          out = xcv[P2] + a.omega_j * cdiv(gv[P2] - Hx, D);
         }
       }
-      a.y[rhs * N + idx] = out;
+      Y[idx] = out;
       if (MODE == M_RESID) nrm2 += (double)abs2(out);
     }
-    wm = w0;
-    w0 = wp;
-    kap_prev = kap_cur;
-    g_prev = g_cur;
-    xc_prev = xc_cur;
-    dinv_prev = dinv_cur;
+  };
+
+  for (int k0 = 0; k0 < nplanes; k0 += NSTAGE) {
+    // each step returns early past the last plane (uniform across the CTA)
+    if (k0 + 0 < nplanes) step(std::integral_constant<int, 0>{}, k0 + 0);
+    if (k0 + 1 < nplanes) step(std::integral_constant<int, 1>{}, k0 + 1);
+    if (k0 + 2 < nplanes) step(std::integral_constant<int, 2>{}, k0 + 2);
+    if (k0 + 3 < nplanes) step(std::integral_constant<int, 3>{}, k0 + 3);
+    if (k0 + 4 < nplanes) step(std::integral_constant<int, 4>{}, k0 + 4);
+    if (k0 + 5 < nplanes) step(std::integral_constant<int, 5>{}, k0 + 5);
   }
   cp_wait<0>();
 
@@ -434,8 +459,8 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
 
 // PATH 0: interior (shell) tiles only; 1: PML tiles only; 2: either, chosen per tile.
 template <class R, int MODE, int OP, int PATH>
-__global__ void __launch_bounds__(NT, (PATH == 0 && sizeof(R) == 4) ? 4 : 1) k_fwd(StencilCall<R> a, int zblock,
-                                                                                   TileMap tm) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) k_fwd(StencilCall<R> a, int zblock,
+                                                                                      TileMap tm) {
   __shared__ cx<R> sX[NSTAGE][PLANE];
   __shared__ R sK[NSTAGE][(MODE == M_J2) ? PLANE : 1];
   __shared__ cx<R> sY1[(MODE == M_J2) ? PLANE : 1];
@@ -674,7 +699,7 @@ static int choose_zblock(int nx, int ny, int nz, int nrhs) {
 // Grids of at least this many nodes split interior and PML tiles into two
 // launches (each kernel then carries only its own path's registers); smaller
 // grids, where launch latency dominates, use one launch choosing per tile.
-constexpr long long kSplitNodes = 4LL << 20;
+constexpr long long kSplitNodes = 1LL << 20;
 
 struct FwdPlan {
   int zb, nzb, TXT, TYT;
