@@ -69,6 +69,17 @@ struct TableView {
   R ds, inv_ds;
 };
 
+// The four power-basis coefficients of one function on one segment (the table
+// is 16-byte aligned: one 128-bit load for float, two for double).
+__device__ __forceinline__ void load_coef4(const float* p, float& c0, float& c1, float& c2, float& c3) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  c0 = v.x; c1 = v.y; c2 = v.z; c3 = v.w;
+}
+__device__ __forceinline__ void load_coef4(const double* p, double& c0, double& c1, double& c2, double& c3) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  c0 = a.x; c1 = a.y; c2 = b.x; c3 = b.y;
+}
+
 // Evaluate functions [F0, F0+NF) at eta (eta already clamped to [0, 0.4]).
 template <class R, int F0, int NF>
 __device__ __forceinline__ void table_eval(const R* __restrict__ tab, int nseg, R ds, R inv_ds, R eta, R* out) {
@@ -77,7 +88,11 @@ __device__ __forceinline__ void table_eval(const R* __restrict__ tab, int nseg, 
   R u = eta - (R)seg * ds;
   const R* c = tab + (seg * kNumFn + F0) * 4;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) out[f] = c[4 * f] + u * (c[4 * f + 1] + u * (c[4 * f + 2] + u * c[4 * f + 3]));
+  for (int f = 0; f < NF; ++f) {
+    R c0, c1, c2, c3;
+    load_coef4(c + 4 * f, c0, c1, c2, c3);
+    out[f] = c0 + u * (c1 + u * (c2 + u * c3));
+  }
 }
 
 // Same, also returning d/deta (for the gradient).

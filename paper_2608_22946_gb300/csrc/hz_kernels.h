@@ -38,6 +38,7 @@ struct StencilCall {
   const cx<R>* x = nullptr;     // APPLY/RESID: x; J2/J1: g; JSWEEP: current iterate y
   const cx<R>* g = nullptr;     // RESID/JSWEEP: right-hand side
   const cx<R>* base = nullptr;  // J2: out = base + J2(g) when non-null
+  const cx<R>* dinv = nullptr;  // J2 (forward): 1/diag of this operator on this level, per node
   cx<R>* y = nullptr;
   int nrhs = 1;
   Reduce red;            // RESID: ||y||^2 per rhs when red.out != nullptr
@@ -135,6 +136,10 @@ void launch_gradient(const LevelView<double>& lv, const TableView<double>& tab, 
 void launch_fold_pml(const double* g_ext, double* g, int nx, int ny, int nz, int n_pml, cudaStream_t s);
 // Interior shell coefficients C_0..C_3 of A at every node (Eq. iofd-shell-coefficients), [m][node].
 void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& tab, double* out, cudaStream_t s);
+// 1 / H_ii for H = A_L (sigma = 0) or B_L at every node of a level (the Jacobi diagonal,
+// Eq. jacobi-map): ell^-2 [2 a4 (abar_x + abar_y + abar_z) - (1 + i sigma) kappa^2 a1].
+template <class R>
+void launch_setup_dinv(const LevelView<R>& lv, const TableView<R>& tab, cx<R> shift, cx<R>* out, cudaStream_t s);
 // Set kernel attributes once per process/device (dynamic shared memory opt-in).
 void init_kernel_attributes();
 

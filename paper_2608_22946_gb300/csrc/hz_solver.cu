@@ -89,6 +89,10 @@ struct Level {
   cx<float>* abar_f[3] = {};
   cx<float>* achk_f[3] = {};
   int plain_lo[3] = {}, plain_hi[3] = {};
+  // 1/diag of the operator each Jacobi map of Algorithm 1 uses on this level
+  // ([0]: A_L, [1]: B_L); complex64 set at creation, complex128 on first use
+  cx<float>* dinv_f[2] = {};
+  cx<double>* dinv_d[2] = {};
 };
 
 template <class R>
@@ -152,6 +156,7 @@ template <> struct Sel<float> {
   static const cx<float>* ab(const Level& L, int a) { return L.abar_f[a]; }
   static const cx<float>* ac(const Level& L, int a) { return L.achk_f[a]; }
   static const float* tab(hz_handle* H) { return H->tab_f; }
+  static const cx<float>* dinv(const Level& L, bool shifted) { return L.dinv_f[shifted ? 1 : 0]; }
   static constexpr int prec = HZ_C64;
 };
 template <> struct Sel<double> {
@@ -160,6 +165,7 @@ template <> struct Sel<double> {
   static const cx<double>* ab(const Level& L, int a) { return L.abar_d[a]; }
   static const cx<double>* ac(const Level& L, int a) { return L.achk_d[a]; }
   static const double* tab(hz_handle* H) { return H->tab_d; }
+  static const cx<double>* dinv(const Level& L, bool shifted) { return L.dinv_d[shifted ? 1 : 0]; }
   static constexpr int prec = HZ_C128;
 };
 
@@ -251,6 +257,24 @@ TableView<R> tview(hz_handle* H) {
   return t;
 }
 
+// Jacobi diagonals used by Algorithm 1: A_h on level 0, B_2h and B_4h (Eq. jacobi-map).
+template <class R>
+void compute_dinv(hz_handle* H, cx<R>* (&d0)[2], cx<R>* (&d1)[2], cx<R>* (&d2)[2]) {
+  const cx<R> one = mkc<R>((R)1, (R)0), sh = mkc<R>((R)1, (R)H->p.sigma);
+  launch_setup_dinv<R>(view<R>(H, 0), tview<R>(H), one, d0[0], H->st);
+  launch_setup_dinv<R>(view<R>(H, 1), tview<R>(H), sh, d1[1], H->st);
+  launch_setup_dinv<R>(view<R>(H, 2), tview<R>(H), sh, d2[1], H->st);
+}
+
+void prepare_dinv_double(hz_handle* H) {
+  if (H->lev[0].dinv_d[0]) return;
+  H->lev[0].dinv_d[0] = H->al.get<cx<double>>(H->lev[0].N);
+  H->lev[1].dinv_d[1] = H->al.get<cx<double>>(H->lev[1].N);
+  H->lev[2].dinv_d[1] = H->al.get<cx<double>>(H->lev[2].N);
+  compute_dinv<double>(H, H->lev[0].dinv_d, H->lev[1].dinv_d, H->lev[2].dinv_d);
+  HZ_CK(cudaGetLastError());
+}
+
 Reduce reducer(hz_handle* H, double* out, double* root = nullptr, double* inv = nullptr) {
   Reduce r;
   r.partial = H->red_partial;
@@ -320,6 +344,8 @@ void jacobi(hz_handle* H, int L, bool shifted, bool adj, const cx<R>* g, cx<R>* 
     HZ_LAUNCHED();
     return;
   }
+  c.dinv = Sel<R>::dinv(H->lev[L], shifted);
+  HZ_REQUIRE(adj || c.dinv, "internal: Jacobi diagonal of this level/operator was not prepared");
   if (nJ == 2) {
     c.x = g;
     c.y = y;
@@ -618,6 +644,9 @@ void plan_all(hz_handle* H, bool count_only) {
       lv.achk_f[a] = al.get<cx<float>>(nn[a]);
     }
   }
+  H->lev[0].dinv_f[0] = al.get<cx<float>>(H->lev[0].N);
+  H->lev[1].dinv_f[1] = al.get<cx<float>>(H->lev[1].N);
+  H->lev[2].dinv_f[1] = al.get<cx<float>>(H->lev[2].N);
   H->tab_d = al.get<double>((size_t)kMaxSeg * kNumFn * 4);
   H->tab_f = al.get<float>((size_t)kMaxSeg * kNumFn * 4);
   const int nr = H->max_nrhs;
@@ -641,12 +670,15 @@ void plan_all(hz_handle* H, bool count_only) {
   }
 }
 
+void prepare_dinv_double(hz_handle* H);
+
 template <class R>
 void ensure_work(hz_handle* H) {
   Work<R>& W = Sel<R>::w(H);
   if (W.ready) return;
   H->al.count_only = false;
   plan_work<R>(H->al, W, H->lev, H->p, H->max_nrhs);
+  if (sizeof(R) == sizeof(double)) prepare_dinv_double(H);
 }
 
 std::vector<double> host_copy(const double* d, int n, cudaStream_t st) {
@@ -956,6 +988,9 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
                                 lv.kap_f, H->st);
       HZ_LAUNCHED();
     }
+    compute_dinv<float>(H, H->lev[0].dinv_f, H->lev[1].dinv_f, H->lev[2].dinv_f);
+    HZ_LAUNCHED();
+    if (H->p.precision == HZ_C128) prepare_dinv_double(H);
     HZ_CK(cudaStreamSynchronize(H->st));
     H->t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     H->st = H->own;
@@ -999,6 +1034,12 @@ hz_status hz_set_params(hz_handle* H, const hz_params* params) {
     }
     drop_graphs(H);
     H->p = *params;
+    // the shift sigma enters the Jacobi diagonals of B_2h, B_4h
+    H->st = H->own;
+    compute_dinv<float>(H, H->lev[0].dinv_f, H->lev[1].dinv_f, H->lev[2].dinv_f);
+    if (H->lev[0].dinv_d[0]) compute_dinv<double>(H, H->lev[0].dinv_d, H->lev[1].dinv_d, H->lev[2].dinv_d);
+    HZ_LAUNCHED();
+    HZ_CK(cudaStreamSynchronize(H->st));
   });
 }
 

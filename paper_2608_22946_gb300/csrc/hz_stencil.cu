@@ -209,8 +209,8 @@ __device__ __forceinline__ void decode_tile(const TileMap& m, int nrhs, int& rhs
 
 template <class R, int MODE, int OP, bool GEN>
 __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, const TileMap& tm, int rhs, int tile_x,
-                                         int tile_y, unsigned bid, cx<R> (*sX)[PLANE], R (*sK)[PLANE], cx<R>* sY1,
-                                         const R* sTab, double* sRed) {
+                                         int tile_y, unsigned bid, cx<R> (*sX)[PLANE], cx<R> (*sD)[PLANE], cx<R>* sY1,
+                                         const R* sTab, double* sRed, R (*sKc)[NT], cx<R> (*sGc)[NT]) {
   const LevelView<R>& L = a.lv;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = tile_x * TX, y0 = tile_y * TY;
@@ -260,6 +260,8 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
       go1 = in1 ? qy * L.nx + qx : 0;
     }
   }
+  const cx<R>* G = (MODE == M_RESID || MODE == M_JSWEEP) ? a.g + rhs * N : nullptr;
+  const cx<R>* DI = a.dinv;  // shared by all right-hand sides
   // shared-memory addresses of this thread's load slots in stage 0
   const unsigned sx0 = (unsigned)__cvta_generic_to_shared(&sX[0][li0]);
   const unsigned sx1 = (unsigned)__cvta_generic_to_shared(&sX[0][li1]);
@@ -275,8 +277,16 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
       asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sx1 + so), "l"(X + (zo + go1)),
                    "n"(sizeof(cx<R>)), "r"(p1 ? (int)sizeof(cx<R>) : 0));
     if (MODE == M_J2) {
-      cp_async<sizeof(R)>(&sK[st][li0], L.kappa + (zo + go0), p0);
-      if (has1) cp_async<sizeof(R)>(&sK[st][li1], L.kappa + (zo + go1), p1);
+      // precomputed 1/diag of every loaded node (zero outside the grid)
+      cp_async<sizeof(cx<R>)>(&sD[st][li0], DI + (zo + go0), p0);
+      if (has1) cp_async<sizeof(cx<R>)>(&sD[st][li1], DI + (zo + go1), p1);
+    }
+    {
+      // the own row's kappa (and right-hand side) ride the same pipeline
+      const bool pc = zin && active;
+      cp_async<sizeof(R)>(&sKc[st][tid], L.kappa + (pc ? zo + col : 0), pc);
+      if (MODE == M_RESID || MODE == M_JSWEEP)
+        cp_async<sizeof(cx<R>)>(&sGc[st][tid], G + (pc ? zo + col : 0), pc);
     }
     cp_commit();
   };
@@ -301,7 +311,6 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   cx<R> xcv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};     // JSWEEP iterate / J2 y1 at the centre
   cx<R> dinvv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};
   double nrm2 = 0.0;
-  const cx<R>* G = (MODE == M_RESID || MODE == M_JSWEEP) ? a.g + rhs * N : nullptr;
   const cx<R>* Bs = a.base ? a.base + rhs * N : nullptr;
 
   auto step = [&](auto Sc, int k) {
@@ -317,53 +326,26 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
     const bool zin = (unsigned)zk < (unsigned)L.nz;
     const cx<R>* P = sX[S];
     if (MODE == M_J2) {
-      // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first sweep)
-      const cx<R> abz = zin ? L.abar[2][zk] : mkc<R>(1, 0);
+      // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first
+      // sweep); g and D^-1 are zero-filled outside the grid, so is y1
       for (int e = tid; e < PLANE; e += NT) {
-        // element e < NT is the thread's own column, the rest the halo ring
-        int lx, ly;
-        if (e < NT) {
-          lx = tx + 1;
-          ly = ty + 1;
-        } else {
-          const int hsel = e - NT;  // 0 .. 2*PW + 2*TY - 1
-          if (hsel < PW) { lx = hsel; ly = 0; }
-          else if (hsel < 2 * PW) { lx = hsel - PW; ly = PH - 1; }
-          else if (hsel < 2 * PW + TY) { lx = 0; ly = hsel - 2 * PW + 1; }
-          else { lx = PW - 1; ly = hsel - 2 * PW - TY + 1; }
-        }
-        const int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
-        const int li = ly * PW + lx;
-        const bool in = zin && (qx >= 0) && (qx < L.nx) && (qy >= 0) && (qy < L.ny);
-        cx<R> y1 = mkc<R>(0, 0), dinv = mkc<R>(0, 0);
-        const cx<R> g = P[li];
-        const R kap = sK[S][li];
-        if (in) {
-          R a1, a4;
-          table_a1a4<R>(sTab, nseg, ds, inv_ds, eta_star(kap), a1, a4);
-          const cx<R> sab = L.abar[0][qx] + L.abar[1][qy] + abz;
-          const cx<R> D = inv_ell2 * ((R)2 * a4 * sab) - (inv_ell2 * kap * kap * a1) * shift;
-          dinv = cinv(D);
-          y1 = a.omega_j * (dinv * g);
-        }
-        sY1[li] = y1;
-        if (e < NT) {
-          gv[C2] = g;
-          kapv[C2] = kap;
-          dinvv[C2] = dinv;
-          xcv[C2] = y1;
-        }
+        const cx<R> g = P[e];
+        const cx<R> dinv = sD[S][e];
+        sY1[e] = a.omega_j * (dinv * g);
+      }
+      {
+        const int li = (ty + 1) * PW + tx + 1;
+        gv[C2] = P[li];
+        dinvv[C2] = sD[S][li];
+        xcv[C2] = a.omega_j * (dinvv[C2] * gv[C2]);
       }
       __syncthreads();
       P = sY1;
     } else {
-      if (active && zin) {
-        const int idx = zk * plane_sz + col;
-        kapv[C2] = L.kappa[idx];
-        if (MODE == M_RESID || MODE == M_JSWEEP) gv[C2] = G[idx];
-        if (MODE == M_JSWEEP) xcv[C2] = P[(ty + 1) * PW + tx + 1];
-      }
+      if (MODE == M_RESID || MODE == M_JSWEEP) gv[C2] = sGc[S][tid];
+      if (MODE == M_JSWEEP) xcv[C2] = P[(ty + 1) * PW + tx + 1];
     }
+    kapv[C2] = sKc[S][tid];
     partials(P, tx + 1, ty + 1, w[CUR]);
 
     if (k >= 2 && active) {
@@ -462,9 +444,11 @@ template <class R, int MODE, int OP, int PATH>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) k_fwd(StencilCall<R> a, int zblock,
                                                                                       TileMap tm) {
   __shared__ cx<R> sX[NSTAGE][PLANE];
-  __shared__ R sK[NSTAGE][(MODE == M_J2) ? PLANE : 1];
+  __shared__ cx<R> sD[(MODE == M_J2) ? NSTAGE : 1][PLANE];
   __shared__ cx<R> sY1[(MODE == M_J2) ? PLANE : 1];
-  __shared__ R sTab[kMaxSeg * kNumFn * 4];
+  __shared__ __align__(16) R sTab[kMaxSeg * kNumFn * 4];
+  __shared__ R sKc[NSTAGE][NT];                                              // kappa of the own column
+  __shared__ cx<R> sGc[(MODE == M_RESID || MODE == M_JSWEEP) ? NSTAGE : 1][NT];  // rhs of the own column
   __shared__ double sRed[32];
   const int tid = threadIdx.y * TX + threadIdx.x;
   for (int i = tid; i < a.tab.nseg * kNumFn * 4; i += NT) sTab[i] = a.tab.coef[i];
@@ -472,18 +456,18 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) 
   int rhs, tile_x, tile_y;
   unsigned bid;
   decode_tile(tm, a.nrhs, rhs, tile_x, tile_y, bid);
-  R(*sKp)[PLANE] = reinterpret_cast<R(*)[PLANE]>(&sK[0][0]);  // only dereferenced in M_J2
+  cx<R>(*sKp)[PLANE] = sD;  // only dereferenced in M_J2
   if constexpr (OP == OP_Q || PATH == 0) {
-    fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
+    fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
   } else if constexpr (PATH == 1) {
-    fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
+    fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
   } else {
     const LevelView<R>& L = a.lv;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
                        (y0 + TY - 1 <= L.plain_hi[1]);
-    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
-    else fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed);
+    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
+    else fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
   }
 }
 

@@ -933,3 +933,31 @@ void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& t
 }
 
 }  // namespace hz
+
+namespace hz {
+
+template <class R>
+__global__ void k_setup_dinv(LevelView<R> L, TableView<R> T, cx<R> shift, cx<R>* __restrict__ out) {
+  const long long N = L.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.nx), y = (int)((i / L.nx) % L.ny), z = (int)(i / ((long long)L.nx * L.ny));
+    const R kap = L.kappa[i];
+    R av[5];
+    table_eval<R, 0, 5>(T.coef, T.nseg, T.ds, T.inv_ds, eta_star(kap), av);
+    const cx<R> sab = L.abar[0][x] + L.abar[1][y] + L.abar[2][z];
+    const cx<R> D = L.inv_ell2 * ((R)2 * av[3] * sab) - (L.inv_ell2 * kap * kap * av[0]) * shift;
+    out[i] = cinv(D);
+  }
+}
+
+template <class R>
+void launch_setup_dinv(const LevelView<R>& lv, const TableView<R>& tab, cx<R> shift, cx<R>* out, cudaStream_t s) {
+  count_launch();
+  k_setup_dinv<R><<<vec_blocks(lv.N), VB, 0, s>>>(lv, tab, shift, out);
+}
+template void launch_setup_dinv<float>(const LevelView<float>&, const TableView<float>&, cx<float>, cx<float>*,
+                                       cudaStream_t);
+template void launch_setup_dinv<double>(const LevelView<double>&, const TableView<double>&, cx<double>, cx<double>*,
+                                        cudaStream_t);
+
+}  // namespace hz
