@@ -91,6 +91,9 @@ typedef struct {
   double inner_tol;    /* HZ_C64 only: floor of the relative tolerance of each
                           complex64 correction solve inside the refinement loop */
   int max_refine;      /* HZ_C64 only: cap on refinement passes */
+  int autotune;        /* nonzero: hz_create times the forward stencil on every level for a
+                          set of z-block sizes (planes per thread block) and keeps the
+                          fastest; zero: a fixed heuristic */
 } hz_params;
 
 typedef struct {
@@ -100,13 +103,14 @@ typedef struct {
   double t_setup;      /* seconds, per-level coefficients and tables */
   double t_solve;      /* seconds */
   size_t device_bytes; /* device memory held by the handle */
+  int zblock[3];       /* z-block of the forward stencil per level (autotuned or heuristic) */
 } hz_stats;
 
 typedef struct hz_handle hz_handle;
 
 /* Table 4 defaults (Sec. 6.1): m_out 5, m_h 2 / nJ_h 2 / w_h 0.8, c_2h 2,
  * m_2h 10, nJ_2h 2 / w_2h 0.8, m_4h 4 / nJ_4h 2 / w_4h 0.2, sigma 0.9,
- * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8. */
+ * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8, autotune 1. */
 void hz_default_params(hz_params* p);
 
 /* Create a solver for one frequency and velocity model.

@@ -43,15 +43,18 @@ class HzParams(ctypes.Structure):
                 ("nJ_2h", ctypes.c_int), ("m_4h", ctypes.c_int), ("nJ_4h", ctypes.c_int),
                 ("w_h", ctypes.c_double), ("w_2h", ctypes.c_double), ("w_4h", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):
     _fields_ = [("pc_calls", ctypes.c_int), ("refine_passes", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("t_setup", ctypes.c_double), ("t_solve", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("t_setup", ctypes.c_double), ("t_solve", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("zblock", ctypes.c_int * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["zblock"] = list(self.zblock)
+        return d
 
 
 _lib = None

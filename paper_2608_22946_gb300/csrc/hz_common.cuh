@@ -131,6 +131,7 @@ struct LevelView {
   const cx<R>* achk[3];
   int plain_lo[3], plain_hi[3];
   R inv_ell2;                     // 1 / ell^2
+  int zblock;                     // planes per CTA of the forward stencil (0: heuristic)
 };
 
 // ----------------------------------------------------------------------------

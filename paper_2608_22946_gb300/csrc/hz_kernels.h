@@ -46,7 +46,7 @@ struct StencilCall {
 
 template <class R>
 void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s);
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs);
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
 
 // Grid transfers (Eq. full-weighting, Eq. linear-prolongation).
 template <class R>

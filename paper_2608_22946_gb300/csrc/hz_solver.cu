@@ -93,6 +93,7 @@ struct Level {
   // ([0]: A_L, [1]: B_L); complex64 set at creation, complex128 on first use
   cx<float>* dinv_f[2] = {};
   cx<double>* dinv_d[2] = {};
+  int zblock = 0;  // forward-stencil planes per thread block (autotuned; 0: heuristic)
 };
 
 template <class R>
@@ -245,6 +246,7 @@ LevelView<R> view(hz_handle* H, int L) {
     v.plain_hi[a] = lv.plain_hi[a];
   }
   v.inv_ell2 = (R)(1.0 / (lv.ell * lv.ell));
+  v.zblock = lv.zblock;
   return v;
 }
 template <class R>
@@ -681,6 +683,50 @@ void ensure_work(hz_handle* H) {
   if (sizeof(R) == sizeof(double)) prepare_dinv_double(H);
 }
 
+// Launch-shape autotuner: on every level, time the forward stencil (A_L apply,
+// nrhs = max_nrhs, the hierarchy's precision) for a set of z-block sizes on two
+// workspace vectors and keep the fastest.  Runs once, at creation.
+template <class R>
+void autotune_zblocks(hz_handle* H) {
+  Work<R>& W = Sel<R>::w(H);
+  const int nr = H->max_nrhs;
+  cx<R>* src[3] = {W.Vo, W.Vk, W.P};
+  cudaEvent_t e0, e1;
+  HZ_CK(cudaEventCreate(&e0));
+  HZ_CK(cudaEventCreate(&e1));
+  const int cand[] = {4, 6, 8, 10, 12, 16, 22, 28, 34, 46, 64};
+  for (int L = 0; L < 3; ++L) {
+    Level& lv = H->lev[L];
+    const long long n = lv.N * nr;
+    launch_zero<R>(src[L], n, H->st);
+    HZ_LAUNCHED();
+    float best_t = 1e30f;
+    int best = 0;
+    for (int zb : cand) {
+      if (zb > lv.nz && zb != cand[0]) continue;
+      lv.zblock = zb;
+      StencilCall<R> c = call<R>(H, L, false, nr);
+      c.x = src[L];
+      c.y = src[L] + n;  // the next basis vector of the same workspace
+      launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);  // warm-up
+      HZ_CK(cudaEventRecord(e0, H->st));
+      for (int rep = 0; rep < 3; ++rep) launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);
+      HZ_CK(cudaEventRecord(e1, H->st));
+      HZ_LAUNCHED();
+      HZ_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      HZ_CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_t) {
+        best_t = ms;
+        best = zb;
+      }
+    }
+    lv.zblock = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 std::vector<double> host_copy(const double* d, int n, cudaStream_t st) {
   std::vector<double> h(n);
   HZ_CK(cudaMemcpyAsync(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -912,6 +958,7 @@ void hz_default_params(hz_params* p) {
   p->precision = HZ_C64;
   p->inner_tol = 1e-5;
   p->max_refine = 8;
+  p->autotune = 1;
 }
 
 const char* hz_last_error(const hz_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -991,6 +1038,10 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     compute_dinv<float>(H, H->lev[0].dinv_f, H->lev[1].dinv_f, H->lev[2].dinv_f);
     HZ_LAUNCHED();
     if (H->p.precision == HZ_C128) prepare_dinv_double(H);
+    if (H->p.autotune) {
+      if (H->p.precision == HZ_C64) autotune_zblocks<float>(H);
+      else autotune_zblocks<double>(H);
+    }
     HZ_CK(cudaStreamSynchronize(H->st));
     H->t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     H->st = H->own;
@@ -1147,6 +1198,7 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
       stats->t_setup = H->t_setup;
       stats->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       stats->device_bytes = H->al.bytes;
+      for (int L = 0; L < 3; ++L) stats->zblock[L] = H->lev[L].zblock;
     }
     noconv = !(tot.rel <= H->p.tol);
   });
@@ -1242,6 +1294,7 @@ hz_status helmholtz_adjoint_grad(hz_handle* H, const hz_source* src, int nsrc, c
       stats->t_setup = H->t_setup;
       stats->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       stats->device_bytes = H->al.bytes;
+      for (int L = 0; L < 3; ++L) stats->zblock[L] = H->lev[L].zblock;
     }
     noconv = !(tot.rel <= H->p.tol);
   });
@@ -1303,7 +1356,7 @@ extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int p
     HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
     HZ_REQUIRE(nrhs <= kResidStaticMaxRhs, "nrhs exceeds the static scratch limit of 64 right-hand sides");
     const Level& lv = H->lev[level];
-    const long long need = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs) * nrhs;
+    const long long need = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs, lv.zblock) * nrhs;
     HZ_REQUIRE(need <= kResidStaticPartials,
                "grid too large for the static scratch (" + std::to_string(need) + " block partial sums > " +
                    std::to_string(kResidStaticPartials) + ")");

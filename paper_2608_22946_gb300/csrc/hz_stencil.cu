@@ -57,7 +57,9 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // ----------------------------------------------------------------------------
 template <class R, bool GEN> struct Part;
 template <class R> struct Part<R, false> { cx<R> c, e, k; };
-template <class R> struct Part<R, true> { cx<R> c, ex, ey, k, gx, gy, kx, ky; };
+// PML tiles: e = ex + ey and d = ex - ey (x and y neighbours), k corners, g* and k*
+// antisymmetric first differences along x and y
+template <class R> struct Part<R, true> { cx<R> c, e, d, k, gx, gy, kx, ky; };
 
 template <class R>
 __device__ __forceinline__ void zero_part(Part<R, false>& o) {
@@ -65,7 +67,7 @@ __device__ __forceinline__ void zero_part(Part<R, false>& o) {
 }
 template <class R>
 __device__ __forceinline__ void zero_part(Part<R, true>& o) {
-  o.c = o.ex = o.ey = o.k = o.gx = o.gy = o.kx = o.ky = mkc<R>(0, 0);
+  o.c = o.e = o.d = o.k = o.gx = o.gy = o.kx = o.ky = mkc<R>(0, 0);
 }
 
 template <class R>
@@ -89,8 +91,9 @@ __device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R,
   cx<R> m1 = r1[-1], c1 = r1[0], p1 = r1[1];
   cx<R> m2 = r2[-1], c2 = r2[0], p2 = r2[1];
   o.c = c1;
-  o.ex = m1 + p1;
-  o.ey = c0 + c2;
+  const cx<R> ex = m1 + p1, ey = c0 + c2;
+  o.e = ex + ey;
+  o.d = ex - ey;
   o.k = (m0 + p0) + (m2 + p2);
   o.gx = p1 - m1;
   o.gy = c2 - c0;
@@ -118,26 +121,28 @@ __device__ __forceinline__ cx<R> stiff_mass(const Part<R, false>& m, const Part<
   return S12 + abz * S3 + acz * D3;
 }
 
+// General row (PML tiles).  With sb = (abar_x + abar_y)/2 and db = (abar_x - abar_y)/2,
+// abar_x S_1 + abar_y S_2 = sb (S_1 + S_2) + db (S_1 - S_2), where S_1 + S_2 is the
+// shell combination of e and S_1 - S_2 = (a4 + 2 a5/4) d_0 + (a5/4 + 2 b/4)(d_- + d_+).
 template <class R>
 __device__ __forceinline__ cx<R> stiff_mass(const Part<R, true>& m, const Part<R, true>& o, const Part<R, true>& p,
-                                            const R* a, cx<R> abx, cx<R> acx, cx<R> aby, cx<R> acy, cx<R> abz,
+                                            const R* a, cx<R> sb, cx<R> db, cx<R> acx, cx<R> acy, cx<R> abz,
                                             cx<R> acz, cx<R>& Mv) {
   const R a1 = a[0], a2 = a[1], a3 = a[2], a4 = a[3], a5 = a[4];
   const R q5 = a5 * (R)0.25, qb = ((R)1 - a4 - a5) * (R)0.25;
   const R w1 = a2 * (R)(1.0 / 6.0), w2 = a3 * (R)(1.0 / 12.0), w3 = ((R)1 - a1 - a2 - a3) * (R)0.125;
-  cx<R> T3m = a4 * m.c + q5 * (m.ex + m.ey) + qb * m.k;
-  cx<R> T30 = a4 * o.c + q5 * (o.ex + o.ey) + qb * o.k;
-  cx<R> T3p = a4 * p.c + q5 * (p.ex + p.ey) + qb * p.k;
+  cx<R> T3m = a4 * m.c + q5 * m.e + qb * m.k;
+  cx<R> T30 = a4 * o.c + q5 * o.e + qb * o.k;
+  cx<R> T3p = a4 * p.c + q5 * p.e + qb * p.k;
   cx<R> S3 = (T3p + T3m) - (R)2 * T30;
   cx<R> D3 = T3p - T3m;
-  cx<R> S1 = a4 * (o.ex - (R)2 * o.c) + q5 * (o.k - (R)2 * o.ey) + q5 * ((m.ex + p.ex) - (R)2 * (m.c + p.c)) +
-             qb * ((m.k + p.k) - (R)2 * (m.ey + p.ey));
-  cx<R> S2 = a4 * (o.ey - (R)2 * o.c) + q5 * (o.k - (R)2 * o.ex) + q5 * ((m.ey + p.ey) - (R)2 * (m.c + p.c)) +
-             qb * ((m.k + p.k) - (R)2 * (m.ex + p.ex));
+  cx<R> S12 = a4 * (o.e - (R)4 * o.c) + q5 * ((R)2 * (o.k - o.e)) + q5 * ((m.e + p.e) - (R)4 * (m.c + p.c)) +
+              qb * ((R)2 * ((m.k + p.k) - (m.e + p.e)));
+  cx<R> Sd = (a4 + (R)2 * q5) * o.d + (q5 + (R)2 * qb) * (m.d + p.d);
   cx<R> D1 = a4 * o.gx + q5 * o.kx + q5 * (m.gx + p.gx) + qb * (m.kx + p.kx);
   cx<R> D2 = a4 * o.gy + q5 * o.ky + q5 * (m.gy + p.gy) + qb * (m.ky + p.ky);
-  Mv = a1 * o.c + w1 * (o.ex + o.ey + m.c + p.c) + w2 * (o.k + m.ex + m.ey + p.ex + p.ey) + w3 * (m.k + p.k);
-  return abx * S1 + acx * D1 + aby * S2 + acy * D2 + abz * S3 + acz * D3;
+  Mv = a1 * o.c + w1 * (o.e + m.c + p.c) + w2 * (o.k + m.e + p.e) + w3 * (m.k + p.k);
+  return sb * S12 + db * Sd + acx * D1 + acy * D2 + abz * S3 + acz * D3;
 }
 
 // Q_h row (Eq. q-operator) from the shell partials.
@@ -240,6 +245,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
     aby = L.abar[1][cyi];
     acy = L.achk[1][cyi];
   }
+  const cx<R> sbxy = (R)0.5 * (abx + aby), dbxy = (R)0.5 * (abx - aby);
 
   // this thread's (at most two) load slots in every plane, fixed for the march
   const bool has1 = tid + NT < PLANE;
@@ -387,7 +393,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         if (!shell_row) {
           const cx<R> abz = L.abar[2][z], acz = L.achk[2][z];
           cx<R> Mv, Ls;
-          if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, abx, acx, aby, acy, abz, acz, Mv);
+          if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, sbxy, dbxy, acx, acy, abz, acz, Mv);
           else Ls = stiff_mass(wm, w0, wp, av, abz, acz, Mv);
           Hx = (-inv_ell2) * Ls - (mk * shift) * Mv;
           sab = abx + aby + abz;
@@ -694,7 +700,7 @@ struct FwdPlan {
 template <class R>
 static FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, int op) {
   FwdPlan p;
-  p.zb = choose_zblock(L.nx, L.ny, L.nz, nrhs);
+  p.zb = L.zblock > 0 ? min(L.zblock, L.nz) : choose_zblock(L.nx, L.ny, L.nz, nrhs);
   p.nzb = (L.nz + p.zb - 1) / p.zb;
   p.TXT = (L.nx + TX - 1) / TX;
   p.TYT = (L.ny + TY - 1) / TY;
@@ -797,8 +803,8 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
 
 // Blocks per right-hand side of a forward stencil launch on this grid (the
 // size of the per-block partial-sum array its reductions need).
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs) {
-  int zb = choose_zblock(nx, ny, nz, nrhs);
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock) {
+  int zb = zblock > 0 ? min(zblock, nz) : choose_zblock(nx, ny, nz, nrhs);
   return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zb - 1) / zb);
 }
 
