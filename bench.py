@@ -261,7 +261,7 @@ def run_gpu(args):
                          "l2": "inputs larger than L2 (each fine complex64 vector 193 MB)"},
               "time_to_solution_s": t_step, "pc_calls": pc, "rel_res": rel,
               "refine_passes": stats[-1]["refine_passes"], "t_setup_s": stats[-1]["t_setup"],
-              "zblock_tuned": stats[-1].get("zblock"),
+              "zblock_tuned": {"rectangle": stats[-1].get("zblock"), "frame": stats[-1].get("zblock_frame")},
               "gpu_launches": int(launches), "clocks": clk.summary()}
 
     if rank == 0:

@@ -103,7 +103,9 @@ typedef struct {
   double t_setup;      /* seconds, per-level coefficients and tables */
   double t_solve;      /* seconds */
   size_t device_bytes; /* device memory held by the handle */
-  int zblock[3];       /* z-block of the forward stencil per level (autotuned or heuristic) */
+  int zblock[3];       /* z-block of the forward stencil per level (autotuned or heuristic):
+                          the whole grid, or the PML-free rectangle of a split launch */
+  int zblock_frame[3]; /* z-block of the PML-frame launch per level (split launches) */
 } hz_stats;
 
 typedef struct hz_handle hz_handle;

@@ -49,11 +49,12 @@ class HzParams(ctypes.Structure):
 class HzStats(ctypes.Structure):
     _fields_ = [("pc_calls", ctypes.c_int), ("refine_passes", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("t_setup", ctypes.c_double), ("t_solve", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("zblock", ctypes.c_int * 3)]
+                ("zblock", ctypes.c_int * 3), ("zblock_frame", ctypes.c_int * 3)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["zblock"] = list(self.zblock)
+        d["zblock_frame"] = list(self.zblock_frame)
         return d
 
 

@@ -132,6 +132,7 @@ struct LevelView {
   int plain_lo[3], plain_hi[3];
   R inv_ell2;                     // 1 / ell^2
   int zblock;                     // planes per CTA of the forward stencil (0: heuristic)
+  int zblock_f;                   // the same for the PML-frame launch (0: as zblock)
 };
 
 // ----------------------------------------------------------------------------

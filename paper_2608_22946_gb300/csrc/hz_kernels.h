@@ -46,7 +46,10 @@ struct StencilCall {
 
 template <class R>
 void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s);
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
+// Smallest z-block (planes per CTA) of a forward stencil launch.
+constexpr int kMinZblock = 4;
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
+                                 int zblock = 0, int zblock_f = 0);
 
 // Grid transfers (Eq. full-weighting, Eq. linear-prolongation).
 template <class R>

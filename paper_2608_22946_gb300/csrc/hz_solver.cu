@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -18,6 +19,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -93,7 +95,8 @@ struct Level {
   // ([0]: A_L, [1]: B_L); complex64 set at creation, complex128 on first use
   cx<float>* dinv_f[2] = {};
   cx<double>* dinv_d[2] = {};
-  int zblock = 0;  // forward-stencil planes per thread block (autotuned; 0: heuristic)
+  int zblock = 0;    // forward-stencil planes per thread block (autotuned; 0: heuristic)
+  int zblock_f = 0;  // the same for the PML-frame launch (0: as zblock)
 };
 
 template <class R>
@@ -247,6 +250,7 @@ LevelView<R> view(hz_handle* H, int L) {
   }
   v.inv_ell2 = (R)(1.0 / (lv.ell * lv.ell));
   v.zblock = lv.zblock;
+  v.zblock_f = lv.zblock_f;
   return v;
 }
 template <class R>
@@ -618,13 +622,21 @@ void level_dims(const hz_grid& g, int L, Level& lv) {
   lv.n_pml = g.n_pml / f;
   lv.N = (long long)lv.nx * lv.ny * lv.nz;
   lv.ell = g.h * f;
+  // PML-free index ranges (the launch layout and its block counts depend on them)
+  const int nn[3] = {g.nx / f, g.ny / f, g.nz / f};
+  std::vector<std::complex<double>> ab, ac;
+  for (int a = 0; a < 3; ++a) pml_axis(nn[a], lv.n_pml, g.gamma_max, ab, ac, lv.plain_lo[a], lv.plain_hi[a]);
 }
 
+// Per-block partial sums: the vector reductions use at most 1216 x 56, a fused
+// stencil reduction one per block at the smallest z-block (4 planes) the
+// launch planner or the autotuner can pick.
 size_t red_partial_size(const Level* lev, int nrhs) {
   size_t m = 1216 * 56;
   for (int L = 0; L < 3; ++L) {
-    size_t t = (size_t)((lev[L].nx + 31) / 32) * ((lev[L].ny + 7) / 8) * ((lev[L].nz + 3) / 4);
-    m = std::max(m, t);
+    const long long t = stencil_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, lev[L].plain_lo, lev[L].plain_hi, 1,
+                                               kMinZblock, kMinZblock);
+    m = std::max(m, (size_t)t);
   }
   return m * nrhs;
 }
@@ -685,26 +697,58 @@ void ensure_work(hz_handle* H) {
 
 // Launch-shape autotuner: on every level, time the forward stencil (A_L apply,
 // nrhs = max_nrhs, the hierarchy's precision) for a set of z-block sizes on two
-// workspace vectors and keep the fastest.  Runs once, at creation.
+// workspace vectors and keep the fastest; where the level splits into the
+// PML-free rectangle and the PML frame, the frame's z-block is then tuned with
+// the rectangle's fixed.  Runs once, at creation.
+// Tuned z-blocks are kept per process, keyed by device, precision, right-hand
+// sides and level shapes, so handles created again for the same problem size
+// skip the timing.
+struct TuneKey {
+  int dev, prec, nrhs, dims[9];
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, prec, nrhs) < std::tie(o.dev, o.prec, o.nrhs) ||
+           (std::tie(dev, prec, nrhs) == std::tie(o.dev, o.prec, o.nrhs) &&
+            std::lexicographical_compare(dims, dims + 9, o.dims, o.dims + 9));
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 6>> g_tune_cache;
+
 template <class R>
 void autotune_zblocks(hz_handle* H) {
   Work<R>& W = Sel<R>::w(H);
   const int nr = H->max_nrhs;
+  TuneKey key{};
+  HZ_CK(cudaGetDevice(&key.dev));
+  key.prec = (int)sizeof(R);
+  key.nrhs = nr;
+  for (int L = 0; L < 3; ++L) {
+    key.dims[3 * L] = H->lev[L].nx;
+    key.dims[3 * L + 1] = H->lev[L].ny;
+    key.dims[3 * L + 2] = H->lev[L].nz * 1024 + H->lev[L].n_pml;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int L = 0; L < 3; ++L) {
+        H->lev[L].zblock = it->second[2 * L];
+        H->lev[L].zblock_f = it->second[2 * L + 1];
+      }
+      return;
+    }
+  }
   cx<R>* src[3] = {W.Vo, W.Vk, W.P};
   cudaEvent_t e0, e1;
   HZ_CK(cudaEventCreate(&e0));
   HZ_CK(cudaEventCreate(&e1));
-  const int cand[] = {4, 6, 8, 10, 12, 16, 22, 28, 34, 46, 64};
+  const int cand[] = {kMinZblock, 6, 8, 10, 12, 16, 22, 28, 34, 46, 64};
   for (int L = 0; L < 3; ++L) {
     Level& lv = H->lev[L];
     const long long n = lv.N * nr;
     launch_zero<R>(src[L], n, H->st);
     HZ_LAUNCHED();
-    float best_t = 1e30f;
-    int best = 0;
-    for (int zb : cand) {
-      if (zb > lv.nz && zb != cand[0]) continue;
-      lv.zblock = zb;
+    auto time_apply = [&]() {
       StencilCall<R> c = call<R>(H, L, false, nr);
       c.x = src[L];
       c.y = src[L] + n;  // the next basis vector of the same workspace
@@ -716,15 +760,37 @@ void autotune_zblocks(hz_handle* H) {
       HZ_CK(cudaEventSynchronize(e1));
       float ms = 0.f;
       HZ_CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_t) {
-        best_t = ms;
-        best = zb;
+      return ms;
+    };
+    const bool split = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock, 64) !=
+                       stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock,
+                                              kMinZblock);
+    for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
+      float best_t = 1e30f;
+      int best = 0;
+      for (int zb : cand) {
+        if (zb > lv.nz && zb != cand[0]) continue;
+        if (pass == 0) lv.zblock = zb;
+        lv.zblock_f = zb;
+        const float ms = time_apply();
+        if (ms < best_t) {
+          best_t = ms;
+          best = zb;
+        }
       }
+      if (pass == 0) lv.zblock = best;
+      lv.zblock_f = best;
     }
-    lv.zblock = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  std::array<int, 6> tuned;
+  for (int L = 0; L < 3; ++L) {
+    tuned[2 * L] = H->lev[L].zblock;
+    tuned[2 * L + 1] = H->lev[L].zblock_f;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = tuned;
 }
 
 std::vector<double> host_copy(const double* d, int n, cudaStream_t st) {
@@ -1198,7 +1264,10 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
       stats->t_setup = H->t_setup;
       stats->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       stats->device_bytes = H->al.bytes;
-      for (int L = 0; L < 3; ++L) stats->zblock[L] = H->lev[L].zblock;
+      for (int L = 0; L < 3; ++L) {
+        stats->zblock[L] = H->lev[L].zblock;
+        stats->zblock_frame[L] = H->lev[L].zblock_f > 0 ? H->lev[L].zblock_f : H->lev[L].zblock;
+      }
     }
     noconv = !(tot.rel <= H->p.tol);
   });
@@ -1294,7 +1363,10 @@ hz_status helmholtz_adjoint_grad(hz_handle* H, const hz_source* src, int nsrc, c
       stats->t_setup = H->t_setup;
       stats->t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       stats->device_bytes = H->al.bytes;
-      for (int L = 0; L < 3; ++L) stats->zblock[L] = H->lev[L].zblock;
+      for (int L = 0; L < 3; ++L) {
+        stats->zblock[L] = H->lev[L].zblock;
+        stats->zblock_frame[L] = H->lev[L].zblock_f > 0 ? H->lev[L].zblock_f : H->lev[L].zblock;
+      }
     }
     noconv = !(tot.rel <= H->p.tol);
   });
@@ -1356,7 +1428,8 @@ extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int p
     HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
     HZ_REQUIRE(nrhs <= kResidStaticMaxRhs, "nrhs exceeds the static scratch limit of 64 right-hand sides");
     const Level& lv = H->lev[level];
-    const long long need = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs, lv.zblock) * nrhs;
+    const long long need =
+        stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nrhs, lv.zblock, lv.zblock_f) * nrhs;
     HZ_REQUIRE(need <= kResidStaticPartials,
                "grid too large for the static scratch (" + std::to_string(need) + " block partial sums > " +
                    std::to_string(kResidStaticPartials) + ")");

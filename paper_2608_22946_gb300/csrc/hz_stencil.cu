@@ -36,6 +36,19 @@ namespace hz {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int PW = TX + 2, PH = TY + 2, PLANE = PW * PH;
+
+// Column-tile shapes of the forward kernel (NT threads, one column each).  A
+// plane of a tile plus its one-node halo is TX_ + 2 by TY_ + 2 nodes and is
+// loaded with at most two cp.async per thread.
+template <int TX_, int TY_>
+struct TileShape {
+  static constexpr int TXS = TX_, TYS = TY_, PWS = TX_ + 2, PLN = (TX_ + 2) * (TY_ + 2);
+  static_assert(TX_ * TY_ == NT, "one column per thread");
+  static_assert(PLN <= 2 * NT, "two load slots per thread");
+};
+using TileSq = TileShape<TX, TY>;   // the PML-free rectangle; whole small grids
+using TileW = TileShape<64, 4>;     // PML strips below and above the rectangle (all x)
+using TileT = TileShape<4, 64>;     // PML strips left and right of it (its y range)
 constexpr int NSTAGE = 6;   // shared-memory plane ring
 constexpr int PREF = 5;     // planes in flight ahead of the one consumed (NSTAGE - 1)
 
@@ -70,11 +83,11 @@ __device__ __forceinline__ void zero_part(Part<R, true>& o) {
   o.c = o.e = o.d = o.k = o.gx = o.gy = o.kx = o.ky = mkc<R>(0, 0);
 }
 
-template <class R>
+template <int PWS, class R>
 __device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R, false>& o) {
-  const cx<R>* r0 = P + (ly - 1) * PW + lx;
-  const cx<R>* r1 = r0 + PW;
-  const cx<R>* r2 = r1 + PW;
+  const cx<R>* r0 = P + (ly - 1) * PWS + lx;
+  const cx<R>* r1 = r0 + PWS;
+  const cx<R>* r2 = r1 + PWS;
   cx<R> m0 = r0[-1], c0 = r0[0], p0 = r0[1];
   cx<R> m1 = r1[-1], c1 = r1[0], p1 = r1[1];
   cx<R> m2 = r2[-1], c2 = r2[0], p2 = r2[1];
@@ -82,11 +95,11 @@ __device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R,
   o.e = (m1 + p1) + (c0 + c2);
   o.k = (m0 + p0) + (m2 + p2);
 }
-template <class R>
+template <int PWS, class R>
 __device__ __forceinline__ void partials(const cx<R>* P, int lx, int ly, Part<R, true>& o) {
-  const cx<R>* r0 = P + (ly - 1) * PW + lx;
-  const cx<R>* r1 = r0 + PW;
-  const cx<R>* r2 = r1 + PW;
+  const cx<R>* r0 = P + (ly - 1) * PWS + lx;
+  const cx<R>* r1 = r0 + PWS;
+  const cx<R>* r2 = r1 + PWS;
   cx<R> m0 = r0[-1], c0 = r0[0], p0 = r0[1];
   cx<R> m1 = r1[-1], c1 = r1[0], p1 = r1[1];
   cx<R> m2 = r2[-1], c2 = r2[0], p2 = r2[1];
@@ -124,7 +137,7 @@ __device__ __forceinline__ cx<R> stiff_mass(const Part<R, false>& m, const Part<
 // General row (PML tiles).  With sb = (abar_x + abar_y)/2 and db = (abar_x - abar_y)/2,
 // abar_x S_1 + abar_y S_2 = sb (S_1 + S_2) + db (S_1 - S_2), where S_1 + S_2 is the
 // shell combination of e and S_1 - S_2 = (a4 + 2 a5/4) d_0 + (a5/4 + 2 b/4)(d_- + d_+).
-template <class R>
+template <int FORM, class R>
 __device__ __forceinline__ cx<R> stiff_mass(const Part<R, true>& m, const Part<R, true>& o, const Part<R, true>& p,
                                             const R* a, cx<R> sb, cx<R> db, cx<R> acx, cx<R> acy, cx<R> abz,
                                             cx<R> acz, cx<R>& Mv) {
@@ -139,10 +152,11 @@ __device__ __forceinline__ cx<R> stiff_mass(const Part<R, true>& m, const Part<R
   cx<R> S12 = a4 * (o.e - (R)4 * o.c) + q5 * ((R)2 * (o.k - o.e)) + q5 * ((m.e + p.e) - (R)4 * (m.c + p.c)) +
               qb * ((R)2 * ((m.k + p.k) - (m.e + p.e)));
   cx<R> Sd = (a4 + (R)2 * q5) * o.d + (q5 + (R)2 * qb) * (m.d + p.d);
-  cx<R> D1 = a4 * o.gx + q5 * o.kx + q5 * (m.gx + p.gx) + qb * (m.kx + p.kx);
-  cx<R> D2 = a4 * o.gy + q5 * o.ky + q5 * (m.gy + p.gy) + qb * (m.ky + p.ky);
   Mv = a1 * o.c + w1 * (o.e + m.c + p.c) + w2 * (o.k + m.e + p.e) + w3 * (m.k + p.k);
-  return sb * S12 + db * Sd + acx * D1 + acy * D2 + abz * S3 + acz * D3;
+  cx<R> r = sb * S12 + db * Sd + abz * S3 + acz * D3;
+  if constexpr (FORM != 3) r += acx * (a4 * o.gx + q5 * o.kx + q5 * (m.gx + p.gx) + qb * (m.kx + p.kx));
+  if constexpr (FORM != 1) r += acy * (a4 * o.gy + q5 * o.ky + q5 * (m.gy + p.gy) + qb * (m.ky + p.ky));
+  return r;
 }
 
 // Q_h row (Eq. q-operator) from the shell partials.
@@ -171,54 +185,74 @@ __device__ __forceinline__ void table_a1a4(const R* __restrict__ tab, int nseg, 
   a4 = c[12] + u * (c[13] + u * (c[14] + u * c[15]));
 }
 
-// Which tiles a launch covers.  mode 0: the rectangle of tiles starting at
-// (tx0, ty0), ntx wide, gridDim.y high; mode 1: every tile of the TXT x TYT
-// tiling outside the rectangle [txa, txb] x [tya, tyb].  Blocks of all the
-// launches of one operator application share one numbering (bid_offset,
-// nblk_total) so that a fused grid reduction spans them.
+// Which tiles a launch covers.  Rectangle launches (PATH 0 and 2, 32 x 8
+// tiles): tile (t, blockIdx.y) has its origin at (ox + 32 t, oy + 8 blockIdx.y)
+// and writes the columns up to (rx1, ry1).  Frame launches (PATH 1): the PML
+// frame around the PML-free rectangle [px0, px1] x [py0, py1], as rows of
+// 64 x 4 tiles below and above it (full x range) followed by rows of 4 x 64
+// tiles left and right of it (its y range).  The blocks of all the launches of
+// one operator application share one numbering (bid_offset, nblk_total) so
+// that a fused grid reduction spans them.
 struct TileMap {
-  int mode = 0;
-  int tx0 = 0, ty0 = 0, ntx = 1;
-  int TXT = 1, TYT = 1, txa = 0, txb = -1, tya = 0, tyb = -1;
+  int ox = 0, oy = 0, ntx = 1, rx1 = 0, ry1 = 0;
+  int nx = 0, ny = 0, px0 = 0, px1 = -1, py0 = 0, py1 = -1;
+  int nwx = 0, nw_lo = 0, nw_hi = 0;  // 64 x 4 tiles per strip row; tile rows below / above
+  int nty = 0, nt_lo = 0, nt_hi = 0;  // rows of 4 x 64 tiles; tiles left / right per row
+  int count = 0;                      // frame tiles per z-block
   int bid_offset = 0, nblk_total = 1;
 };
 
-__device__ __forceinline__ void decode_tile(const TileMap& m, int nrhs, int& rhs, int& tile_x, int& tile_y,
-                                            unsigned& bid) {
-  rhs = blockIdx.x % nrhs;
-  const int t = blockIdx.x / nrhs;
-  if (m.mode == 0) {
-    tile_x = m.tx0 + t;
-    tile_y = m.ty0 + blockIdx.y;
-    bid = (unsigned)(m.bid_offset + t + m.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
-  } else {
-    const int RW = m.txb - m.txa + 1, RH = m.tyb - m.tya + 1;
-    const int n_top = m.tya * m.TXT, per_row = m.TXT - RW, n_mid = RH * per_row;
-    if (t < n_top) {
-      tile_y = t / m.TXT;
-      tile_x = t - tile_y * m.TXT;
-    } else if (t < n_top + n_mid) {
-      const int u = t - n_top;
-      tile_y = m.tya + u / per_row;
-      const int c = u - (tile_y - m.tya) * per_row;
-      tile_x = c < m.txa ? c : c + RW;
+struct FrameTile {
+  int x0, y0, rx1, ry1;
+  bool wide;
+};
+
+__device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int t) {
+  FrameTile f;
+  const int nw = m.nwx * (m.nw_lo + m.nw_hi);
+  if (t < nw) {
+    const int r = t / m.nwx, c = t - r * m.nwx;
+    f.x0 = c * TileW::TXS;
+    f.rx1 = m.nx - 1;
+    if (r < m.nw_lo) {
+      f.y0 = r * TileW::TYS;
+      f.ry1 = m.py0 - 1;
     } else {
-      const int u = t - n_top - n_mid;
-      tile_y = m.tyb + 1 + u / m.TXT;
-      tile_x = u - (tile_y - m.tyb - 1) * m.TXT;
+      f.y0 = m.py1 + 1 + (r - m.nw_lo) * TileW::TYS;
+      f.ry1 = m.ny - 1;
     }
-    const int count = m.TXT * m.TYT - RW * RH;
-    bid = (unsigned)(m.bid_offset + t + count * blockIdx.z);
+    f.wide = true;
+  } else {
+    const int u = t - nw, per = m.nt_lo + m.nt_hi;
+    const int r = u / per, c = u - r * per;
+    f.y0 = m.py0 + r * TileT::TYS;
+    f.ry1 = m.py1;
+    if (c < m.nt_lo) {
+      f.x0 = c * TileT::TXS;
+      f.rx1 = m.px0 - 1;
+    } else {
+      f.x0 = m.px1 + 1 + (c - m.nt_lo) * TileT::TXS;
+      f.rx1 = m.nx - 1;
+    }
+    f.wide = false;
   }
+  return f;
 }
 
-template <class R, int MODE, int OP, bool GEN>
-__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, const TileMap& tm, int rhs, int tile_x,
-                                         int tile_y, unsigned bid, cx<R> (*sX)[PLANE], cx<R> (*sD)[PLANE], cx<R>* sY1,
+// One CTA: the tile of shape TL with origin (x0, y0), writing the columns up to
+// (rx1, ry1) (both inside the grid), over z-block blockIdx.z.
+// Row forms: 0 shell (x and y outside the PML), 1 PML along x only, 2 general,
+// 3 PML along y only.  Forms 1 and 3 drop the first-difference term of the
+// PML-free axis, whose achk is exactly zero.
+template <class R, int MODE, int OP, int FORM, class TL>
+__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, const TileMap& tm, int rhs, int x0,
+                                         int y0, int rx1, int ry1, unsigned bid, cx<R>* sX, cx<R>* sD, cx<R>* sY1,
                                          const R* sTab, double* sRed, R (*sKc)[NT], cx<R> (*sGc)[NT]) {
+  constexpr int PWS = TL::PWS, PLN = TL::PLN;
+  constexpr bool GEN = FORM != 0;
   const LevelView<R>& L = a.lv;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int x0 = tile_x * TX, y0 = tile_y * TY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int tx = tid % TL::TXS, ty = tid / TL::TXS;
   const int zb0 = blockIdx.z * zblock;
   const int zb1 = min(zb0 + zblock, L.nz);
   const int nplanes = zb1 - zb0 + 2;
@@ -226,7 +260,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   const cx<R>* X = a.x + rhs * N;
   cx<R>* Y = a.y + rhs * N;
   const int gx = x0 + tx, gy = y0 + ty;
-  const bool active = (gx < L.nx) && (gy < L.ny);
+  const bool active = (gx <= rx1) && (gy <= ry1);
   // fields have fewer than 2^31 nodes (checked at creation): 32-bit offsets
   const int col = gy * L.nx + gx;
   const int plane_sz = L.nx * L.ny;
@@ -248,18 +282,18 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   const cx<R> sbxy = (R)0.5 * (abx + aby), dbxy = (R)0.5 * (abx - aby);
 
   // this thread's (at most two) load slots in every plane, fixed for the march
-  const bool has1 = tid + NT < PLANE;
+  const bool has1 = tid + NT < PLN;
   const int li0 = tid, li1 = tid + NT;
   int go0 = 0, go1 = 0;
   bool in0, in1 = false;
   {
-    int ly = li0 / PW, lx = li0 - ly * PW;
+    int ly = li0 / PWS, lx = li0 - ly * PWS;
     int qx = x0 - 1 + lx, qy = y0 - 1 + ly;
     in0 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
     go0 = in0 ? qy * L.nx + qx : 0;
     if (has1) {
-      ly = li1 / PW;
-      lx = li1 - ly * PW;
+      ly = li1 / PWS;
+      lx = li1 - ly * PWS;
       qx = x0 - 1 + lx;
       qy = y0 - 1 + ly;
       in1 = qx >= 0 && qx < L.nx && qy >= 0 && qy < L.ny;
@@ -269,9 +303,9 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   const cx<R>* G = (MODE == M_RESID || MODE == M_JSWEEP) ? a.g + rhs * N : nullptr;
   const cx<R>* DI = a.dinv;  // shared by all right-hand sides
   // shared-memory addresses of this thread's load slots in stage 0
-  const unsigned sx0 = (unsigned)__cvta_generic_to_shared(&sX[0][li0]);
-  const unsigned sx1 = (unsigned)__cvta_generic_to_shared(&sX[0][li1]);
-  constexpr unsigned kStageBytes = PLANE * sizeof(cx<R>);
+  const unsigned sx0 = (unsigned)__cvta_generic_to_shared(sX + li0);
+  const unsigned sx1 = (unsigned)__cvta_generic_to_shared(sX + li1);
+  constexpr unsigned kStageBytes = PLN * sizeof(cx<R>);
   auto issue = [&](int z, int st) {
     const bool zin = (unsigned)z < (unsigned)L.nz;
     const int zo = zin ? z * plane_sz : 0;
@@ -284,8 +318,8 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
                    "n"(sizeof(cx<R>)), "r"(p1 ? (int)sizeof(cx<R>) : 0));
     if (MODE == M_J2) {
       // precomputed 1/diag of every loaded node (zero outside the grid)
-      cp_async<sizeof(cx<R>)>(&sD[st][li0], DI + (zo + go0), p0);
-      if (has1) cp_async<sizeof(cx<R>)>(&sD[st][li1], DI + (zo + go1), p1);
+      cp_async<sizeof(cx<R>)>(sD + st * PLN + li0, DI + (zo + go0), p0);
+      if (has1) cp_async<sizeof(cx<R>)>(sD + st * PLN + li1, DI + (zo + go1), p1);
     }
     {
       // the own row's kappa (and right-hand side) ride the same pipeline
@@ -330,29 +364,29 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
     if (k + PREF < nplanes) issue(zk + PREF, (S + PREF) % NSTAGE);
     else cp_commit();
     const bool zin = (unsigned)zk < (unsigned)L.nz;
-    const cx<R>* P = sX[S];
+    const cx<R>* P = sX + S * PLN;
     if (MODE == M_J2) {
       // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first
       // sweep); g and D^-1 are zero-filled outside the grid, so is y1
-      for (int e = tid; e < PLANE; e += NT) {
+      for (int e = tid; e < PLN; e += NT) {
         const cx<R> g = P[e];
-        const cx<R> dinv = sD[S][e];
+        const cx<R> dinv = sD[S * PLN + e];
         sY1[e] = a.omega_j * (dinv * g);
       }
       {
-        const int li = (ty + 1) * PW + tx + 1;
+        const int li = (ty + 1) * PWS + tx + 1;
         gv[C2] = P[li];
-        dinvv[C2] = sD[S][li];
+        dinvv[C2] = sD[S * PLN + li];
         xcv[C2] = a.omega_j * (dinvv[C2] * gv[C2]);
       }
       __syncthreads();
       P = sY1;
     } else {
       if (MODE == M_RESID || MODE == M_JSWEEP) gv[C2] = sGc[S][tid];
-      if (MODE == M_JSWEEP) xcv[C2] = P[(ty + 1) * PW + tx + 1];
+      if (MODE == M_JSWEEP) xcv[C2] = P[(ty + 1) * PWS + tx + 1];
     }
     kapv[C2] = sKc[S][tid];
-    partials(P, tx + 1, ty + 1, w[CUR]);
+    partials<PWS>(P, tx + 1, ty + 1, w[CUR]);
 
     if (k >= 2 && active) {
       const Part<R, GEN>& wm = w[PP];
@@ -393,7 +427,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         if (!shell_row) {
           const cx<R> abz = L.abar[2][z], acz = L.achk[2][z];
           cx<R> Mv, Ls;
-          if constexpr (GEN) Ls = stiff_mass(wm, w0, wp, av, sbxy, dbxy, acx, acy, abz, acz, Mv);
+          if constexpr (GEN) Ls = stiff_mass<FORM>(wm, w0, wp, av, sbxy, dbxy, acx, acy, abz, acz, Mv);
           else Ls = stiff_mass(wm, w0, wp, av, abz, acz, Mv);
           Hx = (-inv_ell2) * Ls - (mk * shift) * Mv;
           sab = abx + aby + abz;
@@ -445,13 +479,15 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   }
 }
 
-// PATH 0: interior (shell) tiles only; 1: PML tiles only; 2: either, chosen per tile.
+// PATH 0: the PML-free rectangle (shell rows); 1: the PML frame around it
+// (general rows); 2: a whole (small) grid, the row form chosen per tile.
 template <class R, int MODE, int OP, int PATH>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) k_fwd(StencilCall<R> a, int zblock,
                                                                                       TileMap tm) {
-  __shared__ cx<R> sX[NSTAGE][PLANE];
-  __shared__ cx<R> sD[(MODE == M_J2) ? NSTAGE : 1][PLANE];
-  __shared__ cx<R> sY1[(MODE == M_J2) ? PLANE : 1];
+  constexpr int PL = (PATH == 1) ? (TileW::PLN > TileT::PLN ? TileW::PLN : TileT::PLN) : TileSq::PLN;
+  __shared__ __align__(16) cx<R> sX[NSTAGE * PL];
+  __shared__ __align__(16) cx<R> sD[(MODE == M_J2) ? NSTAGE * PL : 1];
+  __shared__ cx<R> sY1[(MODE == M_J2) ? PL : 1];
   __shared__ __align__(16) R sTab[kMaxSeg * kNumFn * 4];
   __shared__ R sKc[NSTAGE][NT];                                              // kappa of the own column
   __shared__ cx<R> sGc[(MODE == M_RESID || MODE == M_JSWEEP) ? NSTAGE : 1][NT];  // rhs of the own column
@@ -459,21 +495,42 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) 
   const int tid = threadIdx.y * TX + threadIdx.x;
   for (int i = tid; i < a.tab.nseg * kNumFn * 4; i += NT) sTab[i] = a.tab.coef[i];
   // (visibility of sTab is ensured by the first __syncthreads of the march)
-  int rhs, tile_x, tile_y;
-  unsigned bid;
-  decode_tile(tm, a.nrhs, rhs, tile_x, tile_y, bid);
-  cx<R>(*sKp)[PLANE] = sD;  // only dereferenced in M_J2
-  if constexpr (OP == OP_Q || PATH == 0) {
-    fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
-  } else if constexpr (PATH == 1) {
-    fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
+  const int rhs = blockIdx.x % a.nrhs;
+  const int t = blockIdx.x / a.nrhs;
+  if constexpr (PATH == 1 && OP != OP_Q) {
+    const FrameTile f = decode_frame(tm, t);
+    const unsigned bid = (unsigned)(tm.bid_offset + t + tm.count * blockIdx.z);
+    if (f.wide) {
+      // strips below / above the rectangle: PML along y only away from the corners
+      const bool xplain = f.x0 >= a.lv.plain_lo[0] && f.x0 + TileW::TXS - 1 <= a.lv.plain_hi[0];
+      if (xplain)
+        fwd_body<R, MODE, OP, 3, TileW>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                        sKc, sGc);
+      else
+        fwd_body<R, MODE, OP, 2, TileW>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                        sKc, sGc);
+    } else {
+      // strips left / right of the rectangle lie in its y range: PML along x only
+      fwd_body<R, MODE, OP, 1, TileT>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                      sKc, sGc);
+    }
   } else {
-    const LevelView<R>& L = a.lv;
-    const int x0 = tile_x * TX, y0 = tile_y * TY;
-    const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
-                       (y0 + TY - 1 <= L.plain_hi[1]);
-    if (plain) fwd_body<R, MODE, OP, false>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
-    else fwd_body<R, MODE, OP, true>(a, zblock, tm, rhs, tile_x, tile_y, bid, sX, sKp, sY1, sTab, sRed, sKc, sGc);
+    const int x0 = tm.ox + t * TX, y0 = tm.oy + (int)blockIdx.y * TY;
+    const unsigned bid = (unsigned)(tm.bid_offset + t + tm.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
+    if constexpr (OP == OP_Q || PATH == 0) {
+      fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                       sKc, sGc);
+    } else {
+      const LevelView<R>& L = a.lv;
+      const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
+                         (y0 + TY - 1 <= L.plain_hi[1]);
+      if (plain)
+        fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                         sKc, sGc);
+      else
+        fwd_body<R, MODE, OP, 2, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                         sKc, sGc);
+    }
   }
 }
 
@@ -681,7 +738,7 @@ static int choose_zblock(int nx, int ny, int nz, int nrhs) {
   long long want = 152LL * 2 * 4;
   long long nzb = (want + tiles - 1) / tiles;
   int zb = (int)((nz + nzb - 1) / nzb);
-  if (zb < 4) zb = 4;
+  if (zb < kMinZblock) zb = kMinZblock;
   if (zb > 64) zb = 64;
   return zb;
 }
@@ -691,67 +748,92 @@ static int choose_zblock(int nx, int ny, int nz, int nrhs) {
 // grids, where launch latency dominates, use one launch choosing per tile.
 constexpr long long kSplitNodes = 1LL << 20;
 
+static int cdiv_i(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
+
+// Launch layout of a forward operator application: one rectangle launch over
+// the whole grid, or (large grids, A/B) the PML-free rectangle of shell rows
+// plus the PML frame around it.
 struct FwdPlan {
-  int zb, nzb, TXT, TYT;
-  bool split;
-  int txa, txb, tya, tyb;
+  int zb = 4, nzb = 1;     // whole grid or PML-free rectangle
+  int zbf = 4, nzbf = 1;   // PML frame
+  bool split = false;
+  int TXT = 1, TYT = 1;  // whole-grid 32 x 8 tiling
+  int RW = 0, RH = 0;    // 32 x 8 tiling of the PML-free rectangle
+  TileMap frame;         // frame tiling (count = frame tiles per z-block)
+  long long blocks() const {
+    return split ? (long long)RW * RH * nzb + (long long)frame.count * nzbf : (long long)TXT * TYT * nzb;
+  }
 };
+
+static FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int zb, int zbf) {
+  FwdPlan p;
+  p.zb = std::min(zb, nz);
+  p.nzb = (nz + p.zb - 1) / p.zb;
+  p.zbf = std::min(zbf > 0 ? zbf : zb, nz);
+  p.nzbf = (nz + p.zbf - 1) / p.zbf;
+  p.TXT = (nx + TX - 1) / TX;
+  p.TYT = (ny + TY - 1) / TY;
+  const int px0 = std::max(plo[0], 0), px1 = std::min(phi[0], nx - 1);
+  const int py0 = std::max(plo[1], 0), py1 = std::min(phi[1], ny - 1);
+  p.split = (op == OP_AB) && (long long)nx * ny * nz >= kSplitNodes && px1 >= px0 && py1 >= py0;
+  if (!p.split) return p;
+  p.RW = cdiv_i(px1 - px0 + 1, TX);
+  p.RH = cdiv_i(py1 - py0 + 1, TY);
+  TileMap& f = p.frame;
+  f.nx = nx;
+  f.ny = ny;
+  f.px0 = px0;
+  f.px1 = px1;
+  f.py0 = py0;
+  f.py1 = py1;
+  f.nwx = cdiv_i(nx, TileW::TXS);
+  f.nw_lo = cdiv_i(py0, TileW::TYS);
+  f.nw_hi = cdiv_i(ny - 1 - py1, TileW::TYS);
+  f.nty = cdiv_i(py1 - py0 + 1, TileT::TYS);
+  f.nt_lo = cdiv_i(px0, TileT::TXS);
+  f.nt_hi = cdiv_i(nx - 1 - px1, TileT::TXS);
+  f.count = f.nwx * (f.nw_lo + f.nw_hi) + f.nty * (f.nt_lo + f.nt_hi);
+  return p;
+}
 
 template <class R>
 static FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, int op) {
-  FwdPlan p;
-  p.zb = L.zblock > 0 ? min(L.zblock, L.nz) : choose_zblock(L.nx, L.ny, L.nz, nrhs);
-  p.nzb = (L.nz + p.zb - 1) / p.zb;
-  p.TXT = (L.nx + TX - 1) / TX;
-  p.TYT = (L.ny + TY - 1) / TY;
-  // interior tile rectangle: tiles whose columns all lie in the PML-free range
-  p.txa = (L.plain_lo[0] + TX - 1) / TX;
-  p.txb = (L.plain_hi[0] + 1) / TX - 1;
-  p.tya = (L.plain_lo[1] + TY - 1) / TY;
-  p.tyb = (L.plain_hi[1] + 1) / TY - 1;
-  p.split = (op == OP_AB) && L.N >= kSplitNodes && p.txb >= p.txa && p.tyb >= p.tya;
-  return p;
+  const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, nrhs);
+  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, op, zb, L.zblock_f);
 }
 
 template <class R, int MODE, int OP>
 static void launch_fwd_t(const StencilCall<R>& c, cudaStream_t s) {
   const LevelView<R>& L = c.lv;
   const FwdPlan p = plan_fwd(L, c.nrhs, OP);
-  const int nblk_total = p.TXT * p.TYT * p.nzb;
+  const int nblk_total = (int)p.blocks();
   if (!p.split) {
     TileMap tm;
-    tm.mode = 0;
     tm.ntx = p.TXT;
+    tm.rx1 = L.nx - 1;
+    tm.ry1 = L.ny - 1;
     tm.nblk_total = nblk_total;
     dim3 grid(p.TXT * c.nrhs, p.TYT, p.nzb);
     count_launch();
     k_fwd<R, MODE, OP, (OP == OP_Q) ? 0 : 2><<<grid, dim3(TX, TY), 0, s>>>(c, p.zb, tm);
     return;
   }
-  const int RW = p.txb - p.txa + 1, RH = p.tyb - p.tya + 1;
   TileMap ti;
-  ti.mode = 0;
-  ti.tx0 = p.txa;
-  ti.ty0 = p.tya;
-  ti.ntx = RW;
+  ti.ox = p.frame.px0;
+  ti.oy = p.frame.py0;
+  ti.ntx = p.RW;
+  ti.rx1 = p.frame.px1;
+  ti.ry1 = p.frame.py1;
   ti.bid_offset = 0;
   ti.nblk_total = nblk_total;
-  TileMap tp;
-  tp.mode = 1;
-  tp.TXT = p.TXT;
-  tp.TYT = p.TYT;
-  tp.txa = p.txa;
-  tp.txb = p.txb;
-  tp.tya = p.tya;
-  tp.tyb = p.tyb;
-  tp.bid_offset = RW * RH * p.nzb;
+  TileMap tp = p.frame;
+  tp.bid_offset = p.RW * p.RH * p.nzb;
   tp.nblk_total = nblk_total;
-  const int ncomp = p.TXT * p.TYT - RW * RH;
   count_launch();
-  k_fwd<R, MODE, OP, 0><<<dim3(RW * c.nrhs, RH, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, ti);
-  if (ncomp > 0) {
+  k_fwd<R, MODE, OP, 0><<<dim3(p.RW * c.nrhs, p.RH, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, ti);
+  if (tp.count > 0) {
     count_launch();
-    k_fwd<R, MODE, OP, 1><<<dim3(ncomp * c.nrhs, 1, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, tp);
+    k_fwd<R, MODE, OP, 1><<<dim3(tp.count * c.nrhs, 1, p.nzbf), dim3(TX, TY), 0, s>>>(c, p.zbf, tp);
   }
 }
 
@@ -803,9 +885,11 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
 
 // Blocks per right-hand side of a forward stencil launch on this grid (the
 // size of the per-block partial-sum array its reductions need).
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock) {
-  int zb = zblock > 0 ? min(zblock, nz) : choose_zblock(nx, ny, nz, nrhs);
-  return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zb - 1) / zb);
+long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
+                                 int zblock, int zblock_f) {
+  const int zb = zblock > 0 ? zblock : choose_zblock(nx, ny, nz, nrhs);
+  const FwdPlan p = plan_layout(nx, ny, nz, plain_lo, plain_hi, OP_AB, zb, zblock_f);
+  return p.blocks();
 }
 
 template <class R, int MODE, int OP>

@@ -22,7 +22,7 @@ static int vec_blocks(long long n) {
 }
 // reduction kernels use fewer, fuller blocks: fewer partial sums to combine
 static int red_blocks(long long n) {
-  long long b = (n + VB * 8 - 1) / (VB * 8);
+  long long b = (n + VB * 4 - 1) / (VB * 4);
   return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 4));
 }
 
@@ -381,25 +381,38 @@ void launch_scale(const cx<R>* w, cx<R>* out, const double* scale, int n, int nr
   k_scale<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(w, out, scale, n, nrhs);
 }
 
-template <class R>
-__global__ void k_combine(const cx<R>* __restrict__ Z, long long zstride, int kn, const double* __restrict__ y, int ld,
+// x = x0 + sum_k y_k Z_k (x0 may be null); the basis size is a template
+// argument so that the loads of all terms are in flight together.
+template <class R, int KN>
+__global__ void k_combine(const cx<R>* __restrict__ Z, long long zstride, const double* __restrict__ y, int ld,
                           const cx<R>* __restrict__ x0, cx<R>* __restrict__ x, int n) {
   __shared__ R sy[2 * KMAX];
   const int rhs = blockIdx.y;
-  if (threadIdx.x < 2 * kn) sy[threadIdx.x] = (R)y[(size_t)rhs * ld * 2 + threadIdx.x];
+  if (threadIdx.x < 2 * KN) sy[threadIdx.x] = (R)y[(size_t)rhs * ld * 2 + threadIdx.x];
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long o = (long long)rhs * n + i;
     cx<R> acc = x0 ? x0[o] : mkc<R>(0, 0);
-    for (int k = 0; k < kn; ++k) acc += mkc<R>(sy[2 * k], sy[2 * k + 1]) * Z[k * zstride + o];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) acc += mkc<R>(sy[2 * k], sy[2 * k + 1]) * Z[k * zstride + o];
     x[o] = acc;
   }
 }
 template <class R>
 void launch_combine(const cx<R>* Z, long long zstride, int kn, const double* y, int ld, const cx<R>* x0, cx<R>* x,
                     int n, int nrhs, cudaStream_t s) {
-  count_launch();
-  k_combine<R><<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(Z, zstride, kn, y, ld, x0, x, n);
+  const dim3 grid(vec_blocks(n), nrhs);
+  switch (kn) {
+#define HZ_KN(K)                                                             \
+  case K:                                                                    \
+    count_launch();                                                          \
+    k_combine<R, K><<<grid, VB, 0, s>>>(Z, zstride, y, ld, x0, x, n); \
+    break;
+    HZ_KN(1) HZ_KN(2) HZ_KN(3) HZ_KN(4) HZ_KN(5) HZ_KN(6) HZ_KN(7) HZ_KN(8) HZ_KN(9) HZ_KN(10) HZ_KN(11)
+    HZ_KN(12) HZ_KN(13) HZ_KN(14) HZ_KN(15) HZ_KN(16)
+#undef HZ_KN
+    default: break;
+  }
 }
 
 template <class R>
@@ -582,9 +595,12 @@ void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, i
 // ----------------------------------------------------------------------------
 // CA-GMRES bottom solve: Gram matrix of [p_0 .. p_s], CholQR, least squares
 // ----------------------------------------------------------------------------
+// The small Cholesky solve runs in one thread of the last block only: the
+// register cap (4 blocks per SM for the usual s = 4) sizes the streaming loop,
+// and whatever the solve does not fit in registers goes to local memory.
 template <class R, int KN>
-__global__ void __launch_bounds__(VB) k_gram(const cx<R>* __restrict__ P, long long pstride, int n, double* y, int ld,
-                                             Reduce red) {
+__global__ void __launch_bounds__(VB, KN <= 5 ? 4 : 2) k_gram(const cx<R>* __restrict__ P, long long pstride, int n,
+                                                             double* y, int ld, Reduce red) {
   constexpr int NG = KN * (KN + 1) / 2;
   constexpr int NV = 2 * NG;
   constexpr int S = KN - 1;

@@ -130,6 +130,38 @@ def test_precond_matches_oracle(hz, prec):
     s.close()
 
 
+def test_split_launch_layout_105(hz):
+    """Grids of at least 2^20 nodes run each forward stencil as two launches:
+    32 x 8 tiles over the PML-free rectangle and 64 x 4 / 4 x 64 tiles over the
+    PML frame around it, whose rows take the x-only, y-only or general PML form.
+    On a 105^3 grid every row of A_h (complex64 and complex128), the fused
+    residual with its norm, and one preconditioner application (Jacobi maps and
+    residuals of the fine level in the same layout) agree with the oracle."""
+    w = W.layered_inclusion(n=104, n_pml=8, nsrc=1)
+    prob, s = make_pair(hz, w, params=hz.default_params(precision=hz.HZ_C64), max_nrhs=1)
+    shape = prob.levels[0].shape
+    assert math.prod(shape) >= 1 << 20
+    x = W.random_complex((1,) + shape, 21)
+    g = W.random_complex((1,) + shape, 22)
+    A = iofd.operator_A(prob, 0, 0.0)
+    ref = A(x[0])[None]
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        y = s.iofd_apply(to_dev(x, dt), op=hz.HZ_OP_A, level=0).cpu().numpy()
+        assert rel_l2(y, ref) <= tol, (dt, rel_l2(y, ref))
+        # row by row: no node is missed or written twice by the two launches
+        row_err = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+        assert row_err.max() <= 1e3 * tol, (dt, row_err.max())
+        r, n2 = s.residual_static(to_dev(g, dt), to_dev(x, dt))
+        rref = g - ref
+        assert rel_l2(r.cpu().numpy(), rref) <= tol
+        assert abs(float(n2[0]) / np.vdot(rref, rref).real - 1) <= 10 * tol
+    M = tg.ThreeGrid(prob)
+    zref = M(g[0])
+    z = s.threegrid_precond(to_dev(g, torch.complex64)).cpu().numpy()
+    assert rel_l2(z[0], zref) <= 2e-4, rel_l2(z[0], zref)
+    s.close()
+
+
 def _oracle_solution(prob, sources, tol=1e-11):
     Q = iofd.operator_Q(prob)
     F = iofd.point_sources(prob, sources)
