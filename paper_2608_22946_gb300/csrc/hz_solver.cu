@@ -753,13 +753,18 @@ void autotune_zblocks(hz_handle* H) {
       c.x = src[L];
       c.y = src[L] + n;  // the next basis vector of the same workspace
       launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);  // warm-up
-      HZ_CK(cudaEventRecord(e0, H->st));
-      for (int rep = 0; rep < 3; ++rep) launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);
-      HZ_CK(cudaEventRecord(e1, H->st));
-      HZ_LAUNCHED();
-      HZ_CK(cudaEventSynchronize(e1));
       float ms = 0.f;
-      HZ_CK(cudaEventElapsedTime(&ms, e0, e1));
+      // short launches (coarse levels) are timed over more repetitions
+      for (int reps : {3, 24}) {
+        HZ_CK(cudaEventRecord(e0, H->st));
+        for (int rep = 0; rep < reps; ++rep) launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);
+        HZ_CK(cudaEventRecord(e1, H->st));
+        HZ_LAUNCHED();
+        HZ_CK(cudaEventSynchronize(e1));
+        HZ_CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= (float)reps;
+        if (ms * reps >= 0.2f) break;
+      }
       return ms;
     };
     const bool split = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock, 64) !=

@@ -29,74 +29,94 @@ static int red_blocks(long long n) {
 // ----------------------------------------------------------------------------
 // transfers
 // ----------------------------------------------------------------------------
+// Both transfer kernels map threads to (x, y) of one plane of one right-hand
+// side (blockIdx.z = rhs * planes + z): no integer division per node, 32-bit
+// offsets within a field (fewer than 2^31 nodes).
+constexpr int TRX = 64, TRY = 4;
+
+// full weighting (Eq. restriction): c = R f, weights (1/4, 1/2, 1/4) per axis
 template <class R>
-__global__ void k_restrict(const cx<R>* __restrict__ f, cx<R>* __restrict__ c, int nxf, int nyf, int nzf, int nrhs) {
+__global__ void __launch_bounds__(TRX * TRY) k_restrict(const cx<R>* __restrict__ f, cx<R>* __restrict__ c, int nxf,
+                                                         int nyf, int nzf) {
   const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
-  const long long Nc = (long long)nxc * nyc * nzc, Nf = (long long)nxf * nyf * nzf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nc * nrhs;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long r = t / Nc, i = t - r * Nc;
-    const int X = (int)(i % nxc), Y = (int)((i / nxc) % nyc), Z = (int)(i / ((long long)nxc * nyc));
-    const cx<R>* F = f + r * Nf;
-    cx<R> acc = mkc<R>(0, 0);
+  const int X = blockIdx.x * TRX + threadIdx.x, Y = blockIdx.y * TRY + threadIdx.y;
+  if (X >= nxc || Y >= nyc) return;
+  const int r = blockIdx.z / nzc, Z = blockIdx.z - r * nzc;
+  const cx<R>* F = f + (long long)r * nxf * nyf * nzf;
+  cx<R> acc = mkc<R>(0, 0);
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int z = 2 * Z + dz;
-      if (z < 0 || z >= nzf) continue;
-      const R wz = dz == 0 ? (R)0.5 : (R)0.25;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = 2 * Z + dz;
+    if (z < 0 || z >= nzf) continue;
+    const R wz = dz == 0 ? (R)0.5 : (R)0.25;
 #pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int y = 2 * Y + dy;
-        if (y < 0 || y >= nyf) continue;
-        const R wzy = wz * (dy == 0 ? (R)0.5 : (R)0.25);
-        const cx<R>* row = F + ((long long)z * nyf + y) * nxf;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = 2 * Y + dy;
+      if (y < 0 || y >= nyf) continue;
+      const R wzy = wz * (dy == 0 ? (R)0.5 : (R)0.25);
+      const cx<R>* row = F + (z * nyf + y) * nxf;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x = 2 * X + dx;
-          if (x < 0 || x >= nxf) continue;
-          acc += (wzy * (dx == 0 ? (R)0.5 : (R)0.25)) * row[x];
-        }
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = 2 * X + dx;
+        if (x < 0 || x >= nxf) continue;
+        acc += (wzy * (dx == 0 ? (R)0.5 : (R)0.25)) * row[x];
       }
     }
-    c[t] = acc;
   }
+  c[(long long)r * nxc * nyc * nzc + (Z * nyc + Y) * nxc + X] = acc;
 }
 
+// trilinear interpolation (Eq. prolongation) added to base: f = base + P c
 template <class R>
-__global__ void k_prolong_add(const cx<R>* __restrict__ c, const cx<R>* __restrict__ base, cx<R>* __restrict__ f,
-                              int nxf, int nyf, int nzf, int nrhs) {
+__global__ void __launch_bounds__(TRX * TRY) k_prolong_add(const cx<R>* __restrict__ c, const cx<R>* __restrict__ base,
+                                                            cx<R>* __restrict__ f, int nxf, int nyf, int nzf) {
   const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
-  const long long Nc = (long long)nxc * nyc * nzc, Nf = (long long)nxf * nyf * nzf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Nf * nrhs;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long r = t / Nf, i = t - r * Nf;
-    const int x = (int)(i % nxf), y = (int)((i / nxf) % nyf), z = (int)(i / ((long long)nxf * nyf));
-    const cx<R>* C = c + r * Nc;
-    const int X0 = x >> 1, Y0 = y >> 1, Z0 = z >> 1;
-    const int ox = x & 1, oy = y & 1, oz = z & 1;
-    cx<R> acc = mkc<R>(0, 0);
-    for (int kz = 0; kz <= oz; ++kz)
-      for (int ky = 0; ky <= oy; ++ky)
-        for (int kx = 0; kx <= ox; ++kx) {
-          const R w = (ox ? (R)0.5 : (R)1) * (oy ? (R)0.5 : (R)1) * (oz ? (R)0.5 : (R)1);
-          acc += w * C[((long long)(Z0 + kz) * nyc + (Y0 + ky)) * nxc + (X0 + kx)];
-        }
-    f[t] = base ? base[t] + acc : acc;
-  }
+  const int x = blockIdx.x * TRX + threadIdx.x, y = blockIdx.y * TRY + threadIdx.y;
+  if (x >= nxf || y >= nyf) return;
+  const int r = blockIdx.z / nzf, z = blockIdx.z - r * nzf;
+  const cx<R>* C = c + (long long)r * nxc * nyc * nzc;
+  // an odd fine index sits halfway between coarse nodes X0 and X0 + 1 (both
+  // inside the grid); an even one on X0 (the second term then has weight 0)
+  const int X0 = x >> 1, Y0 = y >> 1, Z0 = z >> 1;
+  const int ox = x & 1, oy = y & 1, oz = z & 1;
+  const R hx = ox ? (R)0.5 : (R)1, hy = oy ? (R)0.5 : (R)1, hz = oz ? (R)0.5 : (R)1;
+  const R gx = ox ? (R)0.5 : (R)0, gy = oy ? (R)0.5 : (R)0, gz = oz ? (R)0.5 : (R)0;
+  auto row = [&](int Z, int Y) {
+    const cx<R>* p = C + (Z * nyc + Y) * nxc + X0;
+    return hx * p[0] + gx * p[ox];
+  };
+  const cx<R> a0 = hy * row(Z0, Y0) + gy * row(Z0, Y0 + oy);
+  const cx<R> a1 = hy * row(Z0 + oz, Y0) + gy * row(Z0 + oz, Y0 + oy);
+  const cx<R> acc = hz * a0 + gz * a1;
+  const long long t = (long long)r * nxf * nyf * nzf + (z * nyf + y) * nxf + x;
+  f[t] = base ? base[t] + acc : acc;
 }
 
 template <class R>
 void launch_restrict(const cx<R>* fine, cx<R>* coarse, int nxf, int nyf, int nzf, int nrhs, cudaStream_t s) {
-  long long nc = (long long)((nxf - 1) / 2 + 1) * ((nyf - 1) / 2 + 1) * ((nzf - 1) / 2 + 1) * nrhs;
-  count_launch();
-  k_restrict<R><<<vec_blocks(nc), VB, 0, s>>>(fine, coarse, nxf, nyf, nzf, nrhs);
+  const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
+  const long long Nf = (long long)nxf * nyf * nzf, Nc = (long long)nxc * nyc * nzc;
+  const int chunk = std::max(1, 65535 / nzc);  // grid.z limit
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int nr = std::min(chunk, nrhs - r0);
+    const dim3 grid((nxc + TRX - 1) / TRX, (nyc + TRY - 1) / TRY, nzc * nr);
+    count_launch();
+    k_restrict<R><<<grid, dim3(TRX, TRY), 0, s>>>(fine + r0 * Nf, coarse + r0 * Nc, nxf, nyf, nzf);
+  }
 }
 template <class R>
 void launch_prolong_add(const cx<R>* coarse, const cx<R>* base, cx<R>* fine, int nxf, int nyf, int nzf, int nrhs,
                         cudaStream_t s) {
-  long long nf = (long long)nxf * nyf * nzf * nrhs;
-  count_launch();
-  k_prolong_add<R><<<vec_blocks(nf), VB, 0, s>>>(coarse, base, fine, nxf, nyf, nzf, nrhs);
+  const int nxc = (nxf - 1) / 2 + 1, nyc = (nyf - 1) / 2 + 1, nzc = (nzf - 1) / 2 + 1;
+  const long long Nf = (long long)nxf * nyf * nzf, Nc = (long long)nxc * nyc * nzc;
+  const int chunk = std::max(1, 65535 / nzf);  // grid.z limit
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int nr = std::min(chunk, nrhs - r0);
+    const dim3 grid((nxf + TRX - 1) / TRX, (nyf + TRY - 1) / TRY, nzf * nr);
+    count_launch();
+    k_prolong_add<R><<<grid, dim3(TRX, TRY), 0, s>>>(coarse + r0 * Nc, base ? base + r0 * Nf : nullptr,
+                                                      fine + r0 * Nf, nxf, nyf, nzf);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -114,48 +134,124 @@ __device__ __forceinline__ R warp_sum_r(R v) {
   return v;
 }
 
+// Double-single sums for the complex64 path: an unevaluated pair hi + lo of
+// floats added with the error-free two-sum, so the cross-warp and cross-block
+// stages keep about 48 mantissa bits in FP32 arithmetic (the FP64 rate of this
+// GPU is a small fraction of its FP32 rate).  The pair occupies the 8 bytes of
+// a partial-sum slot.
+struct dsf {
+  float hi, lo;
+};
+__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  dsf r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ dsf ds_warp_sum(dsf a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dsf b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a = ds_add(a, b);
+  }
+  return a;
+}
+
 template <class R, int NV>
 __device__ __forceinline__ void block_partials(const R* acc, double* sm /* [VB/32][NV] */, double* partial, int nrhs,
                                                int rhs, unsigned nblk, unsigned blk, int tid) {
   const int lane = tid & 31, w = tid >> 5;
+  float* sf = reinterpret_cast<float*>(sm);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     R x = warp_sum_r<R>(acc[v]);
-    if (lane == 0) sm[w * NV + v] = (double)x;
+    if (lane == 0) {
+      if constexpr (sizeof(R) == sizeof(float)) sf[w * NV + v] = x;
+      else sm[w * NV + v] = (double)x;
+    }
   }
   __syncthreads();
   for (int v = tid; v < NV; v += VB) {
-    double t = 0.0;
+    if constexpr (sizeof(R) == sizeof(float)) {
+      dsf t{0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < VB / 32; ++k) t += sm[k * NV + v];
-    partial[((size_t)v * nrhs + rhs) * nblk + blk] = t;
+      for (int k = 0; k < VB / 32; ++k) t = ds_add(t, dsf{sf[k * NV + v], 0.f});
+      reinterpret_cast<dsf*>(partial)[((size_t)v * nrhs + rhs) * nblk + blk] = t;
+    } else {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < VB / 32; ++k) t += sm[k * NV + v];
+      partial[((size_t)v * nrhs + rhs) * nblk + blk] = t;
+    }
   }
 }
 
 // Stage 2; result for value v in out[v] (shared memory), valid after return.
-template <int NV>
+constexpr int kCombineChunk = 8;
+// Values are combined in chunks of CH so that the accumulators of the last
+// block do not set the register count of the streaming kernels.
+template <class R, int NV>
 __device__ __forceinline__ void combine_partials(const double* partial, int nrhs, int rhs, unsigned nblk,
-                                                 double* sm /* [VB/32][NV] */, double* out, int tid) {
-  double acc[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-  for (unsigned b = tid; b < nblk; b += VB) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(partial + ((size_t)v * nrhs + rhs) * nblk + b);
-  }
+                                                 double* sm /* [VB/32][max(NV, CH)] */, double* out, int tid) {
+  constexpr int CH = kCombineChunk;
   const int lane = tid & 31, w = tid >> 5;
-  __syncthreads();
+#pragma unroll 1
+  for (int v0 = 0; v0 < NV; v0 += CH) {
+    __syncthreads();
+    if constexpr (sizeof(R) == sizeof(float)) {
+      const float2* pp = reinterpret_cast<const float2*>(partial);
+      dsf acc[CH];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double x = warp_sum(acc[v]);
-    if (lane == 0) sm[w * NV + v] = x;
-  }
-  __syncthreads();
-  for (int v = tid; v < NV; v += VB) {
-    double t = 0.0;
+      for (int c = 0; c < CH; ++c) acc[c] = dsf{0.f, 0.f};
+      for (unsigned b = tid; b < nblk; b += VB) {
 #pragma unroll
-    for (int k = 0; k < VB / 32; ++k) t += sm[k * NV + v];
-    out[v] = t;
+        for (int c = 0; c < CH; ++c)
+          if (v0 + c < NV) {
+            const float2 q = __ldcg(pp + ((size_t)(v0 + c) * nrhs + rhs) * nblk + b);
+            acc[c] = ds_add(acc[c], dsf{q.x, q.y});
+          }
+      }
+      dsf* sd = reinterpret_cast<dsf*>(sm);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const dsf x = ds_warp_sum(acc[c]);
+        if (lane == 0) sd[w * CH + c] = x;
+      }
+      __syncthreads();
+      if (tid < CH && v0 + tid < NV) {
+        dsf t{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < VB / 32; ++k) t = ds_add(t, sd[k * CH + tid]);
+        out[v0 + tid] = (double)t.hi + (double)t.lo;
+      }
+    } else {
+      double acc[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+      for (unsigned b = tid; b < nblk; b += VB) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (v0 + c < NV) acc[c] += __ldcg(partial + ((size_t)(v0 + c) * nrhs + rhs) * nblk + b);
+      }
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const double x = warp_sum(acc[c]);
+        if (lane == 0) sm[w * CH + c] = x;
+      }
+      __syncthreads();
+      if (tid < CH && v0 + tid < NV) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < VB / 32; ++k) t += sm[k * CH + tid];
+        out[v0 + tid] = t;
+      }
+    }
   }
   __syncthreads();
 }
@@ -182,7 +278,7 @@ struct CgsArgs {
 template <class R, int KN>
 __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* __restrict__ w, CgsArgs a) {
   constexpr int NV = 2 * KN + 1;
-  __shared__ double sm[(VB / 32) * NV];
+  __shared__ double sm[(VB / 32) * (NV > kCombineChunk ? NV : kCombineChunk)];
   __shared__ double sres[NV];
   __shared__ R scoef[2 * KMAX + 2];
   const int tid = threadIdx.x;
@@ -198,27 +294,46 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
   for (int v = 0; v < NV; ++v) acc[v] = 0;
   cx<R>* W = w + rhs * N;
   const cx<R>* Vr = V + rhs * N;
-  for (long long i = blockIdx.x * (long long)VB + tid; i < N; i += (long long)gridDim.x * VB) {
-    cx<R> wi = W[i];
+  // two elements per iteration, all their loads issued before the arithmetic
+  auto body = [&](const cx<R>* v, cx<R> wi, long long i) {
     if (a.update) {
 #pragma unroll
-      for (int k = 0; k < KN; ++k) wi -= mkc<R>(scoef[2 * k], scoef[2 * k + 1]) * Vr[k * a.vstride + i];
+      for (int k = 0; k < KN; ++k) wi -= mkc<R>(scoef[2 * k], scoef[2 * k + 1]) * v[k];
       W[i] = wi;
     }
     if (a.dots) {
 #pragma unroll
       for (int k = 0; k < KN; ++k) {
-        cx<R> p = cjmul(Vr[k * a.vstride + i], wi);
+        const cx<R> p = cjmul(v[k], wi);
         acc[2 * k] += p.x;
         acc[2 * k + 1] += p.y;
       }
     }
     if (a.norm) acc[2 * KN] += abs2(wi);
+  };
+  const long long stride = (long long)gridDim.x * VB;
+  long long i = blockIdx.x * (long long)VB + tid;
+  for (; i + stride < N; i += 2 * stride) {
+    cx<R> v0[KN > 0 ? KN : 1], v1[KN > 0 ? KN : 1];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      v0[k] = Vr[k * a.vstride + i];
+      v1[k] = Vr[k * a.vstride + i + stride];
+    }
+    const cx<R> w0 = W[i], w1 = W[i + stride];
+    body(v0, w0, i);
+    body(v1, w1, i + stride);
+  }
+  if (i < N) {
+    cx<R> v0[KN > 0 ? KN : 1];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) v0[k] = Vr[k * a.vstride + i];
+    body(v0, W[i], i);
   }
   const unsigned nblk = gridDim.x;
   block_partials<R, NV>(acc, sm, a.red.partial, a.nrhs, rhs, nblk, blockIdx.x, tid);
   if (!last_block_arrive(a.red.count + rhs, nblk, tid)) return;
-  combine_partials<NV>(a.red.partial, a.nrhs, rhs, nblk, sm, sres, tid);
+  combine_partials<R, NV>(a.red.partial, a.nrhs, rhs, nblk, sm, sres, tid);
   if (tid == 0) {
     a.red.count[rhs] = 0;
     double* Hc = a.H ? a.H + ((size_t)rhs * a.hcols + (a.col >= 0 ? a.col : 0)) * a.ld * 2 : nullptr;
@@ -599,12 +714,12 @@ void launch_lsq(const double* H, const double* beta, double* y, int m, int ld, i
 // register cap (4 blocks per SM for the usual s = 4) sizes the streaming loop,
 // and whatever the solve does not fit in registers goes to local memory.
 template <class R, int KN>
-__global__ void __launch_bounds__(VB, KN <= 5 ? 4 : 2) k_gram(const cx<R>* __restrict__ P, long long pstride, int n,
+__global__ void __launch_bounds__(VB) k_gram(const cx<R>* __restrict__ P, long long pstride, int n,
                                                              double* y, int ld, Reduce red) {
   constexpr int NG = KN * (KN + 1) / 2;
   constexpr int NV = 2 * NG;
   constexpr int S = KN - 1;
-  __shared__ double sm[(VB / 32) * NV];
+  __shared__ double sm[(VB / 32) * (NV > kCombineChunk ? NV : kCombineChunk)];
   __shared__ double sres[NV];
   const int tid = threadIdx.x, rhs = blockIdx.y, nrhs = gridDim.y;
   R acc[NV];
@@ -629,86 +744,67 @@ __global__ void __launch_bounds__(VB, KN <= 5 ? 4 : 2) k_gram(const cx<R>* __res
   const unsigned nblk = gridDim.x;
   block_partials<R, NV>(acc, sm, red.partial, nrhs, rhs, nblk, blockIdx.x, tid);
   if (!last_block_arrive(red.count + rhs, nblk, tid)) return;
-  combine_partials<NV>(red.partial, nrhs, rhs, nblk, sm, sres, tid);
+  combine_partials<R, NV>(red.partial, nrhs, rhs, nblk, sm, sres, tid);
   if (tid != 0) return;
   red.count[rhs] = 0;
   // Gram entries G[a][b] = <p_a, p_b>, a <= b, in the order accumulated above
   auto gidx = [](int a, int b) { return a * KN - a * (a - 1) / 2 + (b - a); };
   // normal equations of min || p_0 - sum_k y_k p_{k+1} ||:  G_rr y = g_r0 with
-  // G_rr = [<p_a, p_b>]_{a,b>=1}, g_r0 = [<p_a, p_0>]_{a>=1}; Cholesky G_rr = U^H U
-  double Ur[S][S], Ui[S][S];
-#pragma unroll
-  for (int a = 0; a < S; ++a)
-#pragma unroll
-    for (int b = 0; b < S; ++b) Ur[a][b] = Ui[a][b] = 0.0;
+  // G_rr = [<p_a, p_b>]_{a,b>=1}, g_r0 = [<p_a, p_0>]_{a>=1}; Cholesky G_rr = U^H U.
+  // One thread, small arrays in shared memory and rolled loops: the solve must
+  // not raise the register count of the streaming loop above.
+  __shared__ double sUr[S * S], sUi[S * S], szr[S], szi[S], syr[S], syi[S];
+  for (int a = 0; a < S * S; ++a) sUr[a] = sUi[a] = 0.0;
   double dmax = 0.0;
-#pragma unroll
   for (int a = 1; a < KN; ++a) dmax = fmax(dmax, sres[2 * gidx(a, a)]);
   int rank = S;
-#pragma unroll
-  for (int j = 0; j < S; ++j) {
-    if (j < rank) {
-      double d = sres[2 * gidx(j + 1, j + 1)];
-#pragma unroll
-      for (int k = 0; k < j; ++k) d -= Ur[k][j] * Ur[k][j] + Ui[k][j] * Ui[k][j];
-      if (!(d > 1e-13 * dmax)) {
-        rank = j;  // drop the remaining (numerically dependent) directions
-      } else {
-        const double ujj = sqrt(d), inv = 1.0 / ujj;
-        Ur[j][j] = ujj;
-#pragma unroll
-        for (int b = j + 1; b < S; ++b) {
-          double tr = sres[2 * gidx(j + 1, b + 1)], ti = sres[2 * gidx(j + 1, b + 1) + 1];
-#pragma unroll
-          for (int k = 0; k < j; ++k) {  // t -= conj(U[k][j]) U[k][b]
-            tr -= Ur[k][j] * Ur[k][b] + Ui[k][j] * Ui[k][b];
-            ti -= Ur[k][j] * Ui[k][b] - Ui[k][j] * Ur[k][b];
-          }
-          Ur[j][b] = tr * inv;
-          Ui[j][b] = ti * inv;
-        }
+#pragma unroll 1
+  for (int j = 0; j < rank; ++j) {
+    double d = sres[2 * gidx(j + 1, j + 1)];
+    for (int k = 0; k < j; ++k) d -= sUr[k * S + j] * sUr[k * S + j] + sUi[k * S + j] * sUi[k * S + j];
+    if (!(d > 1e-13 * dmax)) {
+      rank = j;  // drop the remaining (numerically dependent) directions
+      break;
+    }
+    const double ujj = sqrt(d), inv = 1.0 / ujj;
+    sUr[j * S + j] = ujj;
+#pragma unroll 1
+    for (int b = j + 1; b < S; ++b) {
+      double tr = sres[2 * gidx(j + 1, b + 1)], ti = sres[2 * gidx(j + 1, b + 1) + 1];
+      for (int k = 0; k < j; ++k) {  // t -= conj(U[k][j]) U[k][b]
+        tr -= sUr[k * S + j] * sUr[k * S + b] + sUi[k * S + j] * sUi[k * S + b];
+        ti -= sUr[k * S + j] * sUi[k * S + b] - sUi[k * S + j] * sUr[k * S + b];
       }
+      sUr[j * S + b] = tr * inv;
+      sUi[j * S + b] = ti * inv;
     }
   }
   // U^H z = g_r0 (forward), then U y = z (backward); g_r0[a] = <p_{a+1}, p_0> = conj(G[0][a+1])
-  double zr[S], zi[S], yr[S], yi[S];
-#pragma unroll
-  for (int a = 0; a < S; ++a) {
-    zr[a] = zi[a] = yr[a] = yi[a] = 0.0;
-  }
-#pragma unroll
-  for (int a = 0; a < S; ++a) {
-    if (a < rank) {
-      double tr = sres[2 * gidx(0, a + 1)], ti = -sres[2 * gidx(0, a + 1) + 1];
-#pragma unroll
-      for (int k = 0; k < a; ++k) {  // t -= conj(U[k][a]) z_k
-        tr -= Ur[k][a] * zr[k] + Ui[k][a] * zi[k];
-        ti -= Ur[k][a] * zi[k] - Ui[k][a] * zr[k];
-      }
-      zr[a] = tr / Ur[a][a];
-      zi[a] = ti / Ur[a][a];
+  for (int a = 0; a < S; ++a) szr[a] = szi[a] = syr[a] = syi[a] = 0.0;
+#pragma unroll 1
+  for (int a = 0; a < rank; ++a) {
+    double tr = sres[2 * gidx(0, a + 1)], ti = -sres[2 * gidx(0, a + 1) + 1];
+    for (int k = 0; k < a; ++k) {  // t -= conj(U[k][a]) z_k
+      tr -= sUr[k * S + a] * szr[k] + sUi[k * S + a] * szi[k];
+      ti -= sUr[k * S + a] * szi[k] - sUi[k * S + a] * szr[k];
     }
+    szr[a] = tr / sUr[a * S + a];
+    szi[a] = ti / sUr[a * S + a];
   }
-#pragma unroll
-  for (int a = S - 1; a >= 0; --a) {
-    if (a < rank) {
-      double tr = zr[a], ti = zi[a];
-#pragma unroll
-      for (int k = a + 1; k < S; ++k) {
-        if (k < rank) {
-          tr -= Ur[a][k] * yr[k] - Ui[a][k] * yi[k];
-          ti -= Ur[a][k] * yi[k] + Ui[a][k] * yr[k];
-        }
-      }
-      yr[a] = tr / Ur[a][a];
-      yi[a] = ti / Ur[a][a];
+#pragma unroll 1
+  for (int a = rank - 1; a >= 0; --a) {
+    double tr = szr[a], ti = szi[a];
+    for (int k = a + 1; k < rank; ++k) {
+      tr -= sUr[a * S + k] * syr[k] - sUi[a * S + k] * syi[k];
+      ti -= sUr[a * S + k] * syi[k] + sUi[a * S + k] * syr[k];
     }
+    syr[a] = tr / sUr[a * S + a];
+    syi[a] = ti / sUr[a * S + a];
   }
   double* yo = y + (size_t)rhs * ld * 2;
-#pragma unroll
   for (int a = 0; a < S; ++a) {
-    yo[2 * a] = yr[a];
-    yo[2 * a + 1] = yi[a];
+    yo[2 * a] = syr[a];
+    yo[2 * a + 1] = syi[a];
   }
 }
 
