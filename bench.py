@@ -377,6 +377,56 @@ def run_stencil_only(args):
     s.close()
 
 
+# The paper's one-A100 results on its benchmark media (Table 5; complex single
+# precision, 512^3 intervals with 8 PML layers, ppw 6, FGMRES(5) to 1e-4):
+# preconditioner calls, solve time in s, solve time per call in s.
+PAPER_A100_512 = {"homogeneous": (19, 5.512, 0.290), "lens": (12, 4.545, 0.379),
+                  "wedge": (29, 10.863, 0.375), "barrier": (32, 11.970, 0.374)}
+
+
+def run_paper_media(args):
+    """The paper's single-GPU benchmark media at its settings (tol 1e-4,
+    complex64 hierarchy; one FP64 true residual confirms the result), one JSON
+    line per medium with the paper's one-A100 figures beside ours (different
+    hardware: context, not a ratio target)."""
+    import torch
+    import hz_workloads as W
+    import paper_2608_22946_gb300 as hz
+    media = args.media.split(",") if args.media else list(W.PAPER_MEDIA)
+    for kind in media:
+        w = W.paper_medium(kind, n=args.mesh)
+        params = hz.default_params(tol=1e-4, precision=hz.HZ_C64)
+        c_dev = torch.from_numpy(w.c).to("cuda", torch.float64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = hz.Solver(w.n, w.n_pml, w.h, w.omega, c_dev, params=params, max_nrhs=1)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        del c_dev
+        sts = []
+        for it in range(args.warmup + args.steps):
+            _, _, st = s.helmholtz_solve(w.sources)
+            if it >= args.warmup:
+                sts.append(st)
+        t_solve = statistics.median(st["t_solve"] for st in sts)
+        st = sts[-1]
+        pc = st["pc_calls"]
+        row = {"medium": kind, "mesh": w.n, "n_pml": w.n_pml, "nodes": w.N, "tol": 1e-4,
+               "pc_calls": pc, "refine_passes": st["refine_passes"], "rel_res": st["rel_res"],
+               "t_setup_s": st["t_setup"], "t_create_s": t_create, "t_solve_s": t_solve,
+               "solve_per_pc_s": t_solve / max(pc, 1), "device_gib": st["device_bytes"] / 2 ** 30,
+               "zblock": [st["zblock"], st["zblock_frame"]], "precision": "c64 hierarchy + FP64 residual",
+               "data": "synthetic (the paper's medium formula, centre source)"}
+        if w.n == 512 and kind in PAPER_A100_512:
+            p_pc, p_t, p_tpc = PAPER_A100_512[kind]
+            row["paper_1xA100"] = {"pc_calls": p_pc, "t_solve_s": p_t, "solve_per_pc_s": p_tpc,
+                                   "source": "Table 5"}
+        print(json.dumps(row), flush=True)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,8 +439,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--stencil-only", action="store_true")
     ap.add_argument("--max-pc", type=int, default=0, help="profiling only: cap preconditioner calls")
+    ap.add_argument("--paper-media", action="store_true",
+                    help="the paper's benchmark media (homogeneous, lens, wedge, barrier) at tol 1e-4")
+    ap.add_argument("--media", default="", help="comma-separated subset for --paper-media")
+    ap.add_argument("--mesh", type=int, default=512, help="intervals per direction for --paper-media")
     args = ap.parse_args()
-    if args.stencil_only:
+    if args.paper_media:
+        run_paper_media(args)
+    elif args.stencil_only:
         run_stencil_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -194,6 +194,41 @@ def geophysical(n: int = 960, n_pml: int = 24, nsrc: int = 4, ppw: float = 6.0,
     return Workload("geophysical", n, n_pml, h, omega, c, src, seed=seed)
 
 
+PAPER_MEDIA = ("homogeneous", "lens", "wedge", "barrier")
+
+
+def paper_medium(kind: str, n: int = 512, n_pml: int = 8, ppw: float = 6.0) -> Workload:
+    """The benchmark media of the paper's performance study (Sec. 6, "Benchmark
+    Media"; Table 5 uses n = 512, n_pml = 8, ppw_min = 6): unit speed; the
+    converging lens c = 4/3 (1 - exp(-32 |xbar - 1/2|^2) / 2); the three-layer
+    wedge whose interfaces are the planes zbar = 0.4 + 0.1 ybar and
+    zbar = 0.8 - 0.2 ybar (speeds 2, 1.5, 3 from the bottom); the barrier of
+    speed 1e10 on [0,1] x [0.25,0.3] x [0,0.75] in unit speed.  Coordinates are
+    normalised to the physical box; omega puts ppw points in the shortest
+    wavelength; one unit point source at the centre node (reading of "a grid
+    point near the center")."""
+    X, Y, Z = _mesh(n, n_pml)
+    if kind == "homogeneous":
+        c = np.ones_like(X)
+        c_min = 1.0
+    elif kind == "lens":
+        r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+        c = (4.0 / 3.0) * (1.0 - 0.5 * np.exp(-32.0 * r2))
+        c_min = 2.0 / 3.0
+    elif kind == "wedge":
+        c = np.where(Z <= 0.4 + 0.1 * Y, 2.0, np.where(Z <= 0.8 - 0.2 * Y, 1.5, 3.0))
+        c_min = 1.5
+    elif kind == "barrier":
+        inside = (X >= 0.0) & (X <= 1.0) & (Y >= 0.25) & (Y <= 0.3) & (Z >= 0.0) & (Z <= 0.75)
+        c = np.where(inside, 1e10, 1.0)
+        c_min = 1.0
+    else:
+        raise ValueError(f"unknown medium {kind!r}")
+    h, omega = grid_params(n, n_pml, c_min, ppw)
+    src = [(n // 2, n // 2, n // 2, 1.0 + 0.0j)]
+    return Workload(f"paper_{kind}", n, n_pml, h, omega, np.ascontiguousarray(c, dtype=np.float64), src, seed=0)
+
+
 def scaled(kind: str, n: int, n_pml: int, **kw) -> Workload:
     """Same medium recipe at another size (tests use small versions)."""
     f = {"homogeneous": homogeneous, "gaussian_lens": gaussian_lens,
