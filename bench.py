@@ -387,15 +387,18 @@ PAPER_A100_512 = {"homogeneous": (19, 5.512, 0.290), "lens": (12, 4.545, 0.379),
 def run_paper_media(args):
     """The paper's single-GPU benchmark media at its settings (tol 1e-4,
     complex64 hierarchy; one FP64 true residual confirms the result), one JSON
-    line per medium with the paper's one-A100 figures beside ours (different
-    hardware: context, not a ratio target)."""
+    line per medium and tolerance, with the paper's one-A100 figures beside ours
+    (different hardware: context, not a ratio target).  --tols and --precision
+    re-run its tolerance and precision studies (Tables 2 and 3)."""
     import torch
     import hz_workloads as W
     import paper_2608_22946_gb300 as hz
     media = args.media.split(",") if args.media else list(W.PAPER_MEDIA)
-    for kind in media:
+    tols = [float(t) for t in args.tols.split(",")]
+    prec = hz.HZ_C128 if args.precision == "c128" else hz.HZ_C64
+    for kind, tol in [(k, t) for k in media for t in tols]:
         w = W.paper_medium(kind, n=args.mesh)
-        params = hz.default_params(tol=1e-4, precision=hz.HZ_C64)
+        params = hz.default_params(tol=tol, precision=prec)
         c_dev = torch.from_numpy(w.c).to("cuda", torch.float64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -411,13 +414,14 @@ def run_paper_media(args):
         t_solve = statistics.median(st["t_solve"] for st in sts)
         st = sts[-1]
         pc = st["pc_calls"]
-        row = {"medium": kind, "mesh": w.n, "n_pml": w.n_pml, "nodes": w.N, "tol": 1e-4,
+        row = {"medium": kind, "mesh": w.n, "n_pml": w.n_pml, "nodes": w.N, "tol": tol,
                "pc_calls": pc, "refine_passes": st["refine_passes"], "rel_res": st["rel_res"],
                "t_setup_s": st["t_setup"], "t_create_s": t_create, "t_solve_s": t_solve,
                "solve_per_pc_s": t_solve / max(pc, 1), "device_gib": st["device_bytes"] / 2 ** 30,
-               "zblock": [st["zblock"], st["zblock_frame"]], "precision": "c64 hierarchy + FP64 residual",
+               "zblock": [st["zblock"], st["zblock_frame"]],
+               "precision": "c128 throughout" if prec == hz.HZ_C128 else "c64 hierarchy + FP64 residual",
                "data": "synthetic (the paper's medium formula, centre source)"}
-        if w.n == 512 and kind in PAPER_A100_512:
+        if w.n == 512 and kind in PAPER_A100_512 and tol == 1e-4 and prec == hz.HZ_C64:
             p_pc, p_t, p_tpc = PAPER_A100_512[kind]
             row["paper_1xA100"] = {"pc_calls": p_pc, "t_solve_s": p_t, "solve_per_pc_s": p_tpc,
                                    "source": "Table 5"}
@@ -443,6 +447,8 @@ def main():
                     help="the paper's benchmark media (homogeneous, lens, wedge, barrier) at tol 1e-4")
     ap.add_argument("--media", default="", help="comma-separated subset for --paper-media")
     ap.add_argument("--mesh", type=int, default=512, help="intervals per direction for --paper-media")
+    ap.add_argument("--tols", default="1e-4", help="comma-separated tolerances for --paper-media")
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"], help="for --paper-media")
     args = ap.parse_args()
     if args.paper_media:
         run_paper_media(args)
