@@ -350,7 +350,10 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   cx<R> gv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};      // RESID/JSWEEP rhs, J2 raw g
   cx<R> xcv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};     // JSWEEP iterate / J2 y1 at the centre
   cx<R> dinvv[2] = {mkc<R>(0, 0), mkc<R>(0, 0)};
-  double nrm2 = 0.0;
+  // per-thread sum of |r|^2 in the working precision (one FP64 add per node
+  // would cost more than the rest of the row on this GPU's FP64 rate)
+  R nrm2 = 0;
+  const bool want_norm = MODE == M_RESID && a.red.out != nullptr;
   const cx<R>* Bs = a.base ? a.base + rhs * N : nullptr;
 
   auto step = [&](auto Sc, int k) {
@@ -367,19 +370,15 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
     const cx<R>* P = sX + S * PLN;
     if (MODE == M_J2) {
       // y1 = omega D^-1 g on every loaded node of the plane (Eq. jacobi-map, first
-      // sweep); g and D^-1 are zero-filled outside the grid, so is y1
-      for (int e = tid; e < PLN; e += NT) {
-        const cx<R> g = P[e];
-        const cx<R> dinv = sD[S * PLN + e];
-        sY1[e] = a.omega_j * (dinv * g);
-      }
-      {
-        const int li = (ty + 1) * PWS + tx + 1;
-        gv[C2] = P[li];
-        dinvv[C2] = sD[S * PLN + li];
-        xcv[C2] = a.omega_j * (dinvv[C2] * gv[C2]);
-      }
+      // sweep), each thread on its own load slots; g and D^-1 are zero-filled
+      // outside the grid, so is y1
+      sY1[li0] = a.omega_j * (sD[S * PLN + li0] * P[li0]);
+      if (has1) sY1[li1] = a.omega_j * (sD[S * PLN + li1] * P[li1]);
+      const int lc = (ty + 1) * PWS + tx + 1;
+      gv[C2] = P[lc];
+      dinvv[C2] = sD[S * PLN + lc];
       __syncthreads();
+      xcv[C2] = sY1[lc];
       P = sY1;
     } else {
       if (MODE == M_RESID || MODE == M_JSWEEP) gv[C2] = sGc[S][tid];
@@ -445,7 +444,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
         }
       }
       Y[idx] = out;
-      if (MODE == M_RESID) nrm2 += (double)abs2(out);
+      if (MODE == M_RESID && want_norm) nrm2 += abs2(out);
     }
   };
 
@@ -461,7 +460,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   cp_wait<0>();
 
   if (MODE == M_RESID && a.red.out) {
-    double s = block_sum(nrm2, sRed, tid, NT);
+    double s = block_sum((double)nrm2, sRed, tid, NT);
     const unsigned nblk = (unsigned)tm.nblk_total;
     if (tid == 0) a.red.partial[(size_t)rhs * nblk + bid] = s;
     if (last_block_arrive(a.red.count + rhs, nblk, tid)) {
@@ -622,7 +621,8 @@ __global__ void __launch_bounds__(NT) k_adj(StencilCall<R> a, int zblock, int ti
     }
   };
 
-  double nrm2 = 0.0;
+  R nrm2 = 0;
+  const bool want_norm = MODE == M_RESID && a.red.out != nullptr;
   load(zb0 - 1, (zb0 + 2) % 3);
   load(zb0, zb0 % 3);
   for (int z = zb0; z < zb1; ++z) {
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(NT) k_adj(StencilCall<R> a, int zblock, int ti
         out = acc;
       } else if (MODE == M_RESID) {
         out = a.g[rhs * N + idx] - acc;
-        nrm2 += (double)abs2(out);
+        if (want_norm) nrm2 += abs2(out);
       } else {
         const int li = (z % 3) * PLANE + (ty + 1) * PW + (tx + 1);
         const R* p = sP + li * NP;
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(NT) k_adj(StencilCall<R> a, int zblock, int ti
     __syncthreads();
   }
   if (MODE == M_RESID && a.red.out) {
-    double s = block_sum(nrm2, sRed, tid, NT);
+    double s = block_sum((double)nrm2, sRed, tid, NT);
     const unsigned nblk = (unsigned)(tiles_x * gridDim.y * gridDim.z);
     const unsigned bid = (unsigned)(tile_x + tiles_x * (blockIdx.y + gridDim.y * blockIdx.z));
     if (tid == 0) a.red.partial[(size_t)rhs * nblk + bid] = s;

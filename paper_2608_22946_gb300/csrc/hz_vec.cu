@@ -193,64 +193,44 @@ __device__ __forceinline__ void block_partials(const R* acc, double* sm /* [VB/3
 }
 
 // Stage 2; result for value v in out[v] (shared memory), valid after return.
+// One warp per value (warp w takes values w, w + 8, ...): its lanes sum a fixed
+// stride of the block partials, then a warp tree; no block-wide barrier between
+// values and few live accumulators.
 constexpr int kCombineChunk = 8;
-// Values are combined in chunks of CH so that the accumulators of the last
-// block do not set the register count of the streaming kernels.
 template <class R, int NV>
 __device__ __forceinline__ void combine_partials(const double* partial, int nrhs, int rhs, unsigned nblk,
-                                                 double* sm /* [VB/32][max(NV, CH)] */, double* out, int tid) {
-  constexpr int CH = kCombineChunk;
+                                                 double* sm /* unused */, double* out, int tid) {
+  (void)sm;
   const int lane = tid & 31, w = tid >> 5;
+  __syncthreads();
 #pragma unroll 1
-  for (int v0 = 0; v0 < NV; v0 += CH) {
-    __syncthreads();
+  for (int v = w; v < NV; v += VB / 32) {
     if constexpr (sizeof(R) == sizeof(float)) {
-      const float2* pp = reinterpret_cast<const float2*>(partial);
-      dsf acc[CH];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) acc[c] = dsf{0.f, 0.f};
-      for (unsigned b = tid; b < nblk; b += VB) {
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-          if (v0 + c < NV) {
-            const float2 q = __ldcg(pp + ((size_t)(v0 + c) * nrhs + rhs) * nblk + b);
-            acc[c] = ds_add(acc[c], dsf{q.x, q.y});
-          }
+      const float2* pp = reinterpret_cast<const float2*>(partial) + ((size_t)v * nrhs + rhs) * nblk;
+      dsf a{0.f, 0.f}, b{0.f, 0.f};
+      unsigned k = lane;
+      for (; k + 32 < nblk; k += 64) {  // two independent chains
+        const float2 q0 = __ldcg(pp + k), q1 = __ldcg(pp + k + 32);
+        a = ds_add(a, dsf{q0.x, q0.y});
+        b = ds_add(b, dsf{q1.x, q1.y});
       }
-      dsf* sd = reinterpret_cast<dsf*>(sm);
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const dsf x = ds_warp_sum(acc[c]);
-        if (lane == 0) sd[w * CH + c] = x;
+      if (k < nblk) {
+        const float2 q0 = __ldcg(pp + k);
+        a = ds_add(a, dsf{q0.x, q0.y});
       }
-      __syncthreads();
-      if (tid < CH && v0 + tid < NV) {
-        dsf t{0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < VB / 32; ++k) t = ds_add(t, sd[k * CH + tid]);
-        out[v0 + tid] = (double)t.hi + (double)t.lo;
-      }
+      const dsf t = ds_warp_sum(ds_add(a, b));
+      if (lane == 0) out[v] = (double)t.hi + (double)t.lo;
     } else {
-      double acc[CH];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) acc[c] = 0.0;
-      for (unsigned b = tid; b < nblk; b += VB) {
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-          if (v0 + c < NV) acc[c] += __ldcg(partial + ((size_t)(v0 + c) * nrhs + rhs) * nblk + b);
+      const double* pp = partial + ((size_t)v * nrhs + rhs) * nblk;
+      double a = 0.0, b = 0.0;
+      unsigned k = lane;
+      for (; k + 32 < nblk; k += 64) {
+        a += __ldcg(pp + k);
+        b += __ldcg(pp + k + 32);
       }
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const double x = warp_sum(acc[c]);
-        if (lane == 0) sm[w * CH + c] = x;
-      }
-      __syncthreads();
-      if (tid < CH && v0 + tid < NV) {
-        double t = 0.0;
-#pragma unroll
-        for (int k = 0; k < VB / 32; ++k) t += sm[k * CH + tid];
-        out[v0 + tid] = t;
-      }
+      if (k < nblk) a += __ldcg(pp + k);
+      const double t = warp_sum(a + b);
+      if (lane == 0) out[v] = t;
     }
   }
   __syncthreads();
