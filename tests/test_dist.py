@@ -1,0 +1,55 @@
+"""Host-side test of the multi-process path of bench.py: two gloo ranks on the
+CPU run the same barrier / max-over-ranks / aggregation helpers that the GPU
+replicas use with NCCL (replicas share nothing else)."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    w, r, local, pg = bench.dist_setup(world, backend="gloo")
+    assert (w, r, local) == (world, rank, rank)
+    bench.barrier(pg)
+    t_rank = 0.5 + rank          # rank 1 is the slowest
+    t_max = bench.allreduce_max(pg, t_rank)
+    out[rank] = (t_max, bench.aggregate_rate(100.0, w, t_max))
+    bench.barrier(pg)
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_time_and_aggregate():
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        t_max, rate = out[r]
+        assert t_max == 1.5
+        assert rate == pytest.approx(100.0 * 2 / 1.5)
+
+
+def test_single_process_defaults(monkeypatch):
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    import bench
+    w, r, local, pg = bench.dist_setup(1)
+    assert (w, r, pg) == (1, 0, None)
+    assert bench.allreduce_max(pg, 3.0) == 3.0
+    assert bench.aggregate_rate(10.0, 1, 2.0) == 5.0
