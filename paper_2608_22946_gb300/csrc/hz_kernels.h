@@ -42,6 +42,10 @@ struct StencilCall {
   cx<R>* y = nullptr;
   int nrhs = 1;
   Reduce red;            // RESID: ||y||^2 per rhs when red.out != nullptr
+  // optional second stream: the PML-frame launch of a split application runs
+  // on it beside the rectangle launch (fork / join through the two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 template <class R>

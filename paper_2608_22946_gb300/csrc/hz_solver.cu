@@ -123,6 +123,8 @@ struct hz_handle {
   int max_nrhs = 1;
   cudaStream_t st = 0;     // stream the current call enqueues on
   cudaStream_t own = 0;    // non-blocking stream owned by the handle (solves)
+  cudaStream_t side = 0;   // second stream for the PML-frame launches
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   Alloc al;
   Level lev[3];
@@ -301,6 +303,9 @@ StencilCall<R> call(hz_handle* H, int L, bool shifted, int nrhs) {
   c.tab = tview<R>(H);
   c.mass_shift = mkc<R>((R)1, shifted ? (R)H->p.sigma : (R)0);
   c.nrhs = nrhs;
+  c.side = H->side;
+  c.fork = H->ev_fork;
+  c.join = H->ev_join;
   return c;
 }
 
@@ -502,6 +507,13 @@ void precond_enqueue(hz_handle* H, const cx<R>* r, cx<R>* z, int nrhs, bool adj)
   HZ_LAUNCHED();
   // 5: post-smooth S_h(r; z~)
   gmres_cycle<R>(H, 0, adj, r, W.zpre, z, p.m_h, Mh, W.Vs, W.Zs, W.Hs, W.beta_s, W.scale_s, W.ys, nrhs);
+}
+
+void destroy_streams(hz_handle* H) {
+  if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+  if (H->ev_join) cudaEventDestroy(H->ev_join);
+  if (H->side) cudaStreamDestroy(H->side);
+  if (H->own) cudaStreamDestroy(H->own);
 }
 
 void drop_graphs(hz_handle* H) {
@@ -1068,6 +1080,9 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     H->max_nrhs = max_nrhs;
     H->st = (cudaStream_t)stream;
     HZ_CK(cudaStreamCreateWithFlags(&H->own, cudaStreamNonBlocking));
+    HZ_CK(cudaStreamCreateWithFlags(&H->side, cudaStreamNonBlocking));
+    HZ_CK(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
+    HZ_CK(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
     const char* ng = std::getenv("HZ_NO_GRAPH");
     H->use_graphs = !(ng && ng[0] == '1');
     init_kernel_attributes();
@@ -1121,7 +1136,7 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     g_create_error = H->err;
     drop_graphs(H);
     H->al.free_all();
-    if (H->own) cudaStreamDestroy(H->own);
+    destroy_streams(H);
     delete H;
     return st;
   }
@@ -1132,9 +1147,10 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
 hz_status hz_destroy(hz_handle* H) {
   if (!H) return HZ_EINVAL;
   cudaStreamSynchronize(H->own);
+  cudaStreamSynchronize(H->side);
   drop_graphs(H);
   H->al.free_all();
-  if (H->own) cudaStreamDestroy(H->own);
+  destroy_streams(H);
   delete H;
   return HZ_OK;
 }

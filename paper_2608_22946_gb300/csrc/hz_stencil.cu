@@ -829,11 +829,23 @@ static void launch_fwd_t(const StencilCall<R>& c, cudaStream_t s) {
   TileMap tp = p.frame;
   tp.bid_offset = p.RW * p.RH * p.nzb;
   tp.nblk_total = nblk_total;
+  // the two launches are independent (disjoint outputs; a fused norm combines
+  // through its arrival counter): with a side stream they run concurrently
+  const bool fork = c.side && c.fork && c.join && tp.count > 0;
+  cudaStream_t s2 = fork ? c.side : s;
+  if (fork) {
+    cudaEventRecord(c.fork, s);
+    cudaStreamWaitEvent(s2, c.fork, 0);
+  }
   count_launch();
   k_fwd<R, MODE, OP, 0><<<dim3(p.RW * c.nrhs, p.RH, p.nzb), dim3(TX, TY), 0, s>>>(c, p.zb, ti);
   if (tp.count > 0) {
     count_launch();
-    k_fwd<R, MODE, OP, 1><<<dim3(tp.count * c.nrhs, 1, p.nzbf), dim3(TX, TY), 0, s>>>(c, p.zbf, tp);
+    k_fwd<R, MODE, OP, 1><<<dim3(tp.count * c.nrhs, 1, p.nzbf), dim3(TX, TY), 0, s2>>>(c, p.zbf, tp);
+  }
+  if (fork) {
+    cudaEventRecord(c.join, s2);
+    cudaStreamWaitEvent(s, c.join, 0);
   }
 }
 
