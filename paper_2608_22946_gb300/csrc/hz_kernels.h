@@ -71,6 +71,13 @@ struct KrylovCall {
   long long vstride = 0;  // elements between basis vectors
   int kn = 0;            // number of basis vectors involved
   int ld = 0;            // leading dimension of per-rhs scalar rows (complex entries)
+  // selective reorthogonalisation (Arnoldi passes only): per-rhs flag set by
+  // the first pass when its projection leaves more than 1/sqrt(2) of ||w||
+  // (Daniel, Gragg, Kaufman and Stewart's criterion), in which case the
+  // second pass returns at once and the first pass hands its coefficients,
+  // norm and scale to the final update
+  int* skip = nullptr;
+  double* coef_final = nullptr;  // [rhs][ld] complex, read by the final update
 };
 
 // w -= sum_k coef[r][k] V_k  (optional), then dots[r][k] = <V_k, w> (optional),

@@ -124,6 +124,7 @@ struct hz_handle {
   cudaStream_t st = 0;     // stream the current call enqueues on
   cudaStream_t own = 0;    // non-blocking stream owned by the handle (solves)
   cudaStream_t side = 0;   // second stream for the PML-frame launches
+  int* cgs_skip = nullptr; // per rhs: second Gram-Schmidt pass not needed
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   Alloc al;
@@ -405,8 +406,10 @@ void arnoldi_orth(hz_handle* H, int L, int nrhs, cx<R>* V, int j, double* Hm, in
   k.ld = m + 1;
   cx<R>* w = V + (j + 1) * k.vstride;
   Reduce red = reducer(H, nullptr);
-  // pass 1: h1 = V^H w
-  launch_cgs<R>(k, V, w, nullptr, false, true, false, W.coef1, nullptr, EPI_ARNOLDI_FIRST, Hm, j, nullptr, nullptr,
+  k.skip = H->cgs_skip;
+  k.coef_final = W.coef2;
+  // pass 1: h1 = V^H w and ||w||^2 (decides whether pass 2 is needed)
+  launch_cgs<R>(k, V, w, nullptr, false, true, true, W.coef1, nullptr, EPI_ARNOLDI_FIRST, Hm, j, scale, nullptr,
                 red, H->st);
   // pass 2: w -= V h1, then h2 = V^H w and ||w||^2 -> column += h2, subdiagonal, 1/norm
   launch_cgs<R>(k, V, w, W.coef1, true, true, true, W.coef2, nullptr, EPI_ARNOLDI_SECOND, Hm, j, scale, nullptr,
@@ -678,6 +681,7 @@ void plan_all(hz_handle* H, bool count_only) {
   const int nr = H->max_nrhs;
   H->red_partial = al.get<double>(red_partial_size(H->lev, nr));
   H->red_count = al.get<unsigned>(nr);
+  H->cgs_skip = al.get<int>(nr);
   H->s_nrm = al.get<double>(nr);
   H->s_root = al.get<double>(nr);
   H->s_inv = al.get<double>(nr);

@@ -253,6 +253,8 @@ struct CgsArgs {
   double* scale_out;    // [rhs]
   double* beta_out;     // [rhs]
   Reduce red;
+  int* skip;            // see KrylovCall::skip
+  double* coef_final;
 };
 
 template <class R, int KN>
@@ -264,6 +266,10 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
   const int tid = threadIdx.x;
   const int rhs = blockIdx.y;
   const long long N = a.n;
+  // second Arnoldi pass of a right-hand side whose first pass needed no
+  // reorthogonalisation: nothing to do (uniform per block; no block of this
+  // rhs arrives at the reduction, whose counter therefore stays at zero)
+  if (a.epi == EPI_ARNOLDI_SECOND && a.skip && a.skip[rhs]) return;
   if (a.update && tid < KN) {
     scoef[2 * tid] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid];
     scoef[2 * tid + 1] = (R)a.coef[(size_t)rhs * a.ld * 2 + 2 * tid + 1];
@@ -327,14 +333,32 @@ __global__ void __launch_bounds__(VB) k_cgs(const cx<R>* __restrict__ V, cx<R>* 
           }
         if (a.nrm_out) a.nrm_out[rhs] = sres[2 * KN];
         break;
-      case EPI_ARNOLDI_FIRST:
+      case EPI_ARNOLDI_FIRST: {
+        double h1sq = 0.0;
         for (int k = 0; k < KN; ++k) {
           Hc[2 * k] = sres[2 * k];
           Hc[2 * k + 1] = sres[2 * k + 1];
           dout[2 * k] = sres[2 * k];
           dout[2 * k + 1] = sres[2 * k + 1];
+          h1sq += sres[2 * k] * sres[2 * k] + sres[2 * k + 1] * sres[2 * k + 1];
+        }
+        if (a.skip) {
+          // ||w - V h1||^2 = ||w||^2 - ||h1||^2 (orthonormal V); without severe
+          // cancellation (more than half of ||w||^2 left) one pass suffices
+          const double w2 = sres[2 * KN], nu2 = w2 - h1sq;
+          const bool one_pass = nu2 > 0.5 * w2 && nu2 > 1e-300;
+          a.skip[rhs] = one_pass ? 1 : 0;
+          if (one_pass) {
+            const double nu = sqrt(nu2);
+            Hc[2 * KN] = nu;
+            Hc[2 * KN + 1] = 0.0;
+            a.scale_out[rhs] = 1.0 / nu;
+            double* cf = a.coef_final + (size_t)rhs * a.ld * 2;
+            for (int k = 0; k < 2 * KN; ++k) cf[k] = sres[k];
+          }
         }
         break;
+      }
       case EPI_ARNOLDI_SECOND: {
         // second Gram-Schmidt pass: add the correction to the column; the norm
         // of w - V h2 is ||w||^2 - ||h2||^2 for orthonormal V (h2 is tiny)
@@ -421,6 +445,8 @@ void launch_cgs(const KrylovCall& k, const cx<R>* V, cx<R>* w, const double* coe
   a.scale_out = scale_out;
   a.beta_out = beta_out;
   a.red = red;
+  a.skip = k.skip;
+  a.coef_final = k.coef_final;
   switch (k.kn) {
 #define HZ_KN(K) \
   case K: cgs_kn<R, K>(k, V, w, a, s); break;
