@@ -98,7 +98,8 @@ typedef struct {
 
 typedef struct {
   int pc_calls;        /* preconditioner calls = outer FGMRES steps, all passes */
-  int refine_passes;   /* FP64 true-residual evaluations (HZ_C64) */
+  int refine_passes;   /* refinement-loop passes (HZ_C64), each ending in the FP64
+                          true residual; that of the zero initial guess is b itself */
   double rel_res;      /* final ||A v - b|| / ||b||, max over right-hand sides */
   double t_setup;      /* seconds, per-level coefficients and tables */
   double t_solve;      /* seconds */

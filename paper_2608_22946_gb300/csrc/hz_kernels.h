@@ -150,6 +150,8 @@ void launch_gradient(const LevelView<double>& lv, const TableView<double>& tab, 
 void launch_fold_pml(const double* g_ext, double* g, int nx, int ny, int nz, int n_pml, cudaStream_t s);
 // Interior shell coefficients C_0..C_3 of A at every node (Eq. iofd-shell-coefficients), [m][node].
 void launch_shell_coeffs(const LevelView<double>& lv, const TableView<double>& tab, double* out, cudaStream_t s);
+void launch_source_rows(const LevelView<double>& lv, const TableView<double>& tab, const int* idx3,
+                        const double* amp, int nsrc, double scale, cx<double>* b, cudaStream_t s);
 // 1 / H_ii for H = A_L (sigma = 0) or B_L at every node of a level (the Jacobi diagonal,
 // Eq. jacobi-map): ell^-2 [2 a4 (abar_x + abar_y + abar_z) - (1 + i sigma) kappa^2 a1].
 template <class R>

@@ -949,9 +949,24 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
   }
   ensure_work<float>(H);
   // FP64 iterative refinement around complex64 corrections
+  bool x_zero = true;  // the initial guess: its residual is b, whose norms are known
+  std::vector<double> root(nrhs), inv(nrhs);
   for (;;) {
-    resid<double>(H, 0, false, adj, b, x, H->r128, nrhs, reducer(H, H->s_nrm, H->s_root, H->s_inv));
-    std::vector<double> rn = host_copy(H->s_root, nrhs, H->st);
+    std::vector<double> rn;
+    const cx<double>* r = H->r128;
+    if (x_zero) {
+      rn = bn;
+      for (int i = 0; i < nrhs; ++i) {
+        root[i] = bn[i];
+        inv[i] = bn[i] > 1e-300 ? 1.0 / bn[i] : 0.0;
+      }
+      HZ_CK(cudaMemcpyAsync(H->s_root, root.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, H->st));
+      HZ_CK(cudaMemcpyAsync(H->s_inv, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, H->st));
+      r = b;
+    } else {
+      resid<double>(H, 0, false, adj, b, x, H->r128, nrhs, reducer(H, H->s_nrm, H->s_root, H->s_inv));
+      rn = host_copy(H->s_root, nrhs, H->st);
+    }
     ++o.passes;
     double relmax = 0.0, need = 1.0;
     for (int r = 0; r < nrhs; ++r) {
@@ -962,7 +977,7 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     }
     o.rel = relmax;
     if (relmax <= p.tol || o.pc >= p.max_pc || o.passes > p.max_refine) break;
-    launch_c128_to_c64_scaled(H->r128, H->b64, H->s_inv, (int)N, nrhs, H->st);
+    launch_c128_to_c64_scaled(r, H->b64, H->s_inv, (int)N, nrhs, H->st);
     launch_zero<float>(H->x64, N * nrhs, H->st);
     HZ_LAUNCHED();
     std::vector<double> one(nrhs);
@@ -971,11 +986,13 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, inner, p.max_pc, o.pc, true);
     launch_add_c64_to_c128_scaled(H->x64, x, H->s_root, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
+    x_zero = false;
   }
+  HZ_CK(cudaStreamSynchronize(H->st));  // the host norm buffers feed queued copies
   return o;
 }
 
-void upload_sources(hz_handle* H, const hz_source* src, int ns) {
+void upload_source_list(hz_handle* H, const hz_source* src, int ns) {
   std::vector<int> idx(3 * ns);
   std::vector<double> amp(2 * ns);
   for (int s = 0; s < ns; ++s) {
@@ -990,10 +1007,25 @@ void upload_sources(hz_handle* H, const hz_source* src, int ns) {
   }
   HZ_CK(cudaMemcpyAsync(H->src_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, H->st));
   HZ_CK(cudaMemcpyAsync(H->src_amp, amp.data(), amp.size() * sizeof(double), cudaMemcpyHostToDevice, H->st));
+}
+
+// the source field f = amp h^-3 e_{i_s} (Eq. point-source), one per right-hand side
+void upload_sources(hz_handle* H, const hz_source* src, int ns) {
+  upload_source_list(H, src, ns);
   const long long N = H->lev[0].N;
   launch_zero<double>(H->f128, N * ns, H->st);
   launch_point_sources<double>(H->src_idx, H->src_amp, ns, H->lev[0].nx, H->lev[0].ny, H->lev[0].nz,
                                1.0 / (H->g.h * H->g.h * H->g.h), H->f128, H->st);
+  HZ_LAUNCHED();
+}
+
+// b = Q_h f of the point sources directly on their 27-node blocks (no field f)
+void source_rhs(hz_handle* H, const hz_source* src, int ns, cx<double>* b) {
+  upload_source_list(H, src, ns);
+  const long long N = H->lev[0].N;
+  launch_zero<double>(b, N * ns, H->st);
+  launch_source_rows(view<double>(H, 0), tview<double>(H), H->src_idx, H->src_amp, ns,
+                     1.0 / (H->g.h * H->g.h * H->g.h), b, H->st);
   HZ_LAUNCHED();
 }
 
@@ -1272,8 +1304,7 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
     SolveOut tot;
     for (int s0 = 0; s0 < nsrc; s0 += H->max_nrhs) {
       const int ns = std::min(H->max_nrhs, nsrc - s0);
-      upload_sources(H, src + s0, ns);
-      q_apply<double>(H, false, H->f128, H->b128, ns);  // b = Q_h f (Eq. iofd-complete-system)
+      source_rhs(H, src + s0, ns, H->b128);  // b = Q_h f (Eq. iofd-complete-system)
       cx<double>* v = (cx<double>*)v_dev + (size_t)s0 * N;
       SolveOut o = solve_c128(H, H->b128, v, ns, false);
       tot.pc += o.pc;

@@ -877,6 +877,31 @@ void launch_point_sources(const int* idx3, const double* amp, int nsrc, int nx, 
   k_point_sources<R><<<(nsrc + 63) / 64, 64, 0, s>>>(idx3, amp, nsrc, nx, ny, nz, scale, f);
 }
 
+// b = Q_h f for one point source per right-hand side, f = amp h^-3 e_{i_s}
+// (Eq. point-source): row j of Q_h (shell weights of its own eta*, Eq.
+// q-operator) meets the source at offset i_s - j, so b is nonzero only on the
+// in-grid nodes of the 3x3x3 block around i_s.  b must be zero on entry.
+__global__ void k_source_rows(LevelView<double> L, TableView<double> T, const int* __restrict__ idx3,
+                              const double* __restrict__ amp, int nsrc, double scale, cx<double>* __restrict__ b) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 27 * nsrc) return;
+  const int s = t / 27, d = t - 27 * s;
+  const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
+  const int x = idx3[3 * s] + dx, y = idx3[3 * s + 1] + dy, z = idx3[3 * s + 2] + dz;
+  if (x < 0 || x >= L.nx || y < 0 || y >= L.ny || z < 0 || z >= L.nz) return;
+  const long long j = ((long long)z * L.ny + y) * L.nx + x;
+  double bt[3];
+  table_eval<double, 5, 3>(T.coef, T.nseg, T.ds, T.inv_ds, eta_star(L.kappa[j]), bt);
+  const int m = abs(dx) + abs(dy) + abs(dz);
+  const double w = m == 0 ? bt[0] : m == 1 ? bt[1] / 6.0 : m == 2 ? bt[2] / 12.0 : (1.0 - bt[0] - bt[1] - bt[2]) / 8.0;
+  b[(long long)s * L.N + j] = mkc<double>(w * amp[2 * s] * scale, w * amp[2 * s + 1] * scale);
+}
+void launch_source_rows(const LevelView<double>& lv, const TableView<double>& tab, const int* idx3,
+                        const double* amp, int nsrc, double scale, cx<double>* b, cudaStream_t s) {
+  count_launch();
+  k_source_rows<<<(27 * nsrc + 127) / 128, 128, 0, s>>>(lv, tab, idx3, amp, nsrc, scale, b);
+}
+
 template <class R>
 __global__ void k_gather(const cx<R>* u, const int* rec, int nrec, int n, int nrhs, cx<double>* out) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
