@@ -23,7 +23,9 @@
  *     Input and output buffers must not alias unless stated.
  *   - `stream` arguments are cudaStream_t values (0 = legacy default stream)
  *     passed as void*; work is enqueued on it and the call returns without
- *     synchronising unless stated.
+ *     synchronising unless stated.  Part of a stencil application may run on
+ *     a second stream of the handle, forked from `stream` and joined back to
+ *     it with events, so stream order as seen by the caller is unchanged.
  *   - Every entry point returns an hz_status; on failure hz_last_error()
  *     gives a message.  No C++ exception crosses the ABI.  Calls on one
  *     handle must not run concurrently from several host threads.
