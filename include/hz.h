@@ -192,7 +192,9 @@ hz_status threegrid_precond(hz_handle* h, const void* r_dev, void* z_dev, int nr
  * ||A v - b|| / ||b|| <= tol for every source (Sec. 3.3, Eq. relative-residual).
  *   src_host   HOST, nsrc sources; solved in groups of at most max_nrhs.
  *   v_dev      DEVICE complex128, N_0 * nsrc: the IOFD auxiliary field v.
- *   u_dev      DEVICE complex128, N_0 * nsrc, or NULL: the pressure u = Q_h v.
+ *   u_dev      DEVICE complex128, N_0 * nsrc, or NULL: the pressure u = Q_h v
+ *              (evaluated in the hierarchy's precision: complex64 arithmetic
+ *              for HZ_C64, complex128 for HZ_C128).
  *   stats      HOST or NULL.
  * Synchronises.  Returns HZ_ENOCONV (with v, u filled) if max_pc is reached. */
 hz_status helmholtz_solve(hz_handle* h, const hz_source* src_host, int nsrc, void* v_dev, void* u_dev,

@@ -124,6 +124,7 @@ void launch_zero(cx<R>* y, long long n, cudaStream_t s);
 // Mixed precision glue.
 void launch_c128_to_c64_scaled(const cx<double>* in, cx<float>* out, const double* scale, int n, int nrhs,
                                cudaStream_t s);
+void launch_c64_to_c128(const cx<float>* d, cx<double>* x, int n, int nrhs, cudaStream_t s);
 void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const double* scale, int n, int nrhs,
                                    cudaStream_t s);
 template <class R>

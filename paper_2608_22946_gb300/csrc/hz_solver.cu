@@ -1310,7 +1310,18 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
       tot.pc += o.pc;
       tot.passes += o.passes;
       tot.rel = std::max(tot.rel, o.rel);
-      if (u_dev) q_apply<double>(H, false, v, (cx<double>*)u_dev + (size_t)s0 * N, ns);  // u = Q_h v
+      if (u_dev) {
+        cx<double>* u = (cx<double>*)u_dev + (size_t)s0 * N;
+        if (H->p.precision == HZ_C64) {
+          // u = Q_h v in the hierarchy's precision (complex64), widened on output
+          launch_c128_to_c64_scaled(v, H->x64, nullptr, (int)N, ns, H->st);
+          q_apply<float>(H, false, H->x64, H->b64, ns);
+          launch_c64_to_c128(H->b64, u, (int)N, ns, H->st);
+          HZ_LAUNCHED();
+        } else {
+          q_apply<double>(H, false, v, u, ns);  // u = Q_h v
+        }
+      }
     }
     HZ_CK(cudaStreamSynchronize(H->st));
     if (stats) {

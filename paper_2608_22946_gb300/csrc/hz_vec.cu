@@ -571,7 +571,7 @@ void launch_zero(cx<R>* y, long long n, cudaStream_t s) {
 __global__ void k_c128_to_c64(const cx<double>* __restrict__ in, cx<float>* __restrict__ out,
                               const double* __restrict__ scale, int n) {
   const int rhs = blockIdx.y;
-  const double sc = scale[rhs];
+  const double sc = scale ? scale[rhs] : 1.0;  // null: plain narrowing
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     cx<double> v = in[(long long)rhs * n + i];
     out[(long long)rhs * n + i] = mkc<float>((float)(v.x * sc), (float)(v.y * sc));
@@ -583,20 +583,28 @@ void launch_c128_to_c64_scaled(const cx<double>* in, cx<float>* out, const doubl
   k_c128_to_c64<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(in, out, scale, n);
 }
 __global__ void k_add_c64_to_c128(const cx<float>* __restrict__ d, cx<double>* __restrict__ x,
-                                  const double* __restrict__ scale, int n) {
+                                  const double* __restrict__ scale, int n, bool accumulate) {
   const int rhs = blockIdx.y;
-  const double sc = scale[rhs];
+  const double sc = scale ? scale[rhs] : 1.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     cx<float> v = d[(long long)rhs * n + i];
     cx<double>& t = x[(long long)rhs * n + i];
-    t.x += sc * (double)v.x;
-    t.y += sc * (double)v.y;
+    if (accumulate) {
+      t.x += sc * (double)v.x;
+      t.y += sc * (double)v.y;
+    } else {
+      t = mkc<double>(sc * (double)v.x, sc * (double)v.y);
+    }
   }
 }
 void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const double* scale, int n, int nrhs,
                                    cudaStream_t s) {
   count_launch();
-  k_add_c64_to_c128<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(d, x, scale, n);
+  k_add_c64_to_c128<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(d, x, scale, n, true);
+}
+void launch_c64_to_c128(const cx<float>* d, cx<double>* x, int n, int nrhs, cudaStream_t s) {
+  count_launch();
+  k_add_c64_to_c128<<<dim3(vec_blocks(n), nrhs), VB, 0, s>>>(d, x, nullptr, n, false);
 }
 
 // ----------------------------------------------------------------------------
