@@ -12,16 +12,18 @@
 // Coefficients are evaluated per row from kappa = k ell through the cubic
 // Hermite tables at eta* = min(kappa / 2 pi, 0.4) (Eq. iofd-clamped-coordinate).
 //
-// Forward kernel design: a CTA owns a 32 x 8 column tile and marches in z over
-// a block of planes.  Planes (tile + 1-node halo) stream into a 4-deep shared
-// memory ring with cp.async (zero-filled outside the grid, which imposes
-// u = 0).  Each thread reduces the 3x3 in-plane neighbourhood of its column
-// to a few partial sums once per plane and keeps three planes of partials in
-// registers, so every input value is read from shared memory a handful of
-// times instead of 27.  Tiles whose columns are all outside the x/y PML use
-// the 3-partial shell path; the others the 8-partial tensor-product path.
-// Epilogues fuse the residual (with its norm), the two-sweep Jacobi map from
-// zero (Eq. jacobi-map, n_J = 2) and one further Jacobi sweep.
+// Forward kernel design: a CTA of 256 threads owns a tile of columns and
+// marches in z over a block of planes.  Planes (tile + 1-node halo) stream
+// into a 6-stage shared-memory ring with cp.async (zero-filled outside the
+// grid, which imposes u = 0).  Each thread reduces the 3x3 in-plane
+// neighbourhood of its column to a few partial sums once per plane and keeps
+// three planes of partials in registers, so every input value is read from
+// shared memory a handful of times instead of 27.  Large grids are applied in
+// two launches: 32 x 8 tiles over the PML-free rectangle (3-partial shell
+// rows) and 64 x 4 / 4 x 64 tiles over the PML frame around it (tensor-product
+// rows, x-only / y-only / general); small grids in one launch choosing per
+// 32 x 8 tile.  Epilogues fuse the residual (with its norm), the two-sweep
+// Jacobi map from zero (Eq. jacobi-map, n_J = 2) and one further Jacobi sweep.
 //
 // The adjoint kernel applies (H^H x)_i = sum_delta conj(H_{i+delta}(-delta)) x_{i+delta};
 // it needs the neighbours' own coefficients, which it evaluates once per
