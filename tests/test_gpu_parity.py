@@ -216,6 +216,29 @@ def test_batched_solve_equals_single(hz):
     s.close()
 
 
+def test_sources_in_chunks_and_on_the_boundary(hz):
+    """More sources than right-hand-side slots are solved in chunks; sources on
+    a face, an edge and a corner node (their 3x3x3 block of b = Q f partly
+    outside the grid) match the oracle's solutions; an empty source list is
+    rejected."""
+    w = W.gaussian_lens(n=20, n_pml=4)
+    n = w.n
+    sources = [(n // 2, n // 2, n // 2, 1.0 + 0.5j), (0, n // 2, n // 3, -1.0), (n, n, 7, 0.25j),
+               (0, 0, 0, 2.0)]
+    params = hz.default_params(tol=1e-9, precision=hz.HZ_C64)
+    prob, s = make_pair(hz, w, params=params, max_nrhs=3)
+    v, u, st = s.helmholtz_solve(sources)
+    assert v.shape[0] == 4 and st["rel_res"] <= 1e-9
+    vref, Q = _oracle_solution(prob, sources, tol=1e-11)
+    for k in range(4):
+        assert rel_l2(v[k].cpu().numpy(), vref[k]) <= 1e-6, k
+        assert rel_l2(u[k].cpu().numpy(), Q(vref[k])) <= 1e-6, k
+    with pytest.raises(hz.HzError) as e:
+        s.helmholtz_solve([])
+    assert e.value.status == hz.HZ_EINVAL
+    s.close()
+
+
 def test_zero_source_amplitude_gives_zero(hz):
     w = W.homogeneous(n=24, n_pml=4)
     prob, s = make_pair(hz, w)
