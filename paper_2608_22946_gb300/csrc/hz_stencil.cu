@@ -51,6 +51,7 @@ struct TileShape {
 using TileSq = TileShape<TX, TY>;   // the PML-free rectangle; whole small grids
 using TileW = TileShape<64, 4>;     // PML strips below and above the rectangle (all x)
 using TileT = TileShape<4, 64>;     // PML strips left and right of it (its y range)
+using TileG = TileShape<16, 16>;    // whole small grids (coarse levels): fewer idle columns
 constexpr int NSTAGE = 6;   // shared-memory plane ring
 constexpr int PREF = 5;     // planes in flight ahead of the one consumed (NSTAGE - 1)
 
@@ -516,21 +517,23 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) 
                                       sKc, sGc);
     }
   } else {
-    const int x0 = tm.ox + t * TX, y0 = tm.oy + (int)blockIdx.y * TY;
     const unsigned bid = (unsigned)(tm.bid_offset + t + tm.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
     if constexpr (OP == OP_Q || PATH == 0) {
+      const int x0 = tm.ox + t * TX, y0 = tm.oy + (int)blockIdx.y * TY;
       fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
                                        sKc, sGc);
     } else {
+      constexpr int GX = TileG::TXS, GY = TileG::TYS;
+      const int x0 = tm.ox + t * GX, y0 = tm.oy + (int)blockIdx.y * GY;
       const LevelView<R>& L = a.lv;
-      const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
-                         (y0 + TY - 1 <= L.plain_hi[1]);
+      const bool plain = (x0 >= L.plain_lo[0]) && (x0 + GX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
+                         (y0 + GY - 1 <= L.plain_hi[1]);
       if (plain)
-        fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
-                                         sKc, sGc);
+        fwd_body<R, MODE, OP, 0, TileG>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                        sKc, sGc);
       else
-        fwd_body<R, MODE, OP, 2, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
-                                         sKc, sGc);
+        fwd_body<R, MODE, OP, 2, TileG>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+                                        sKc, sGc);
     }
   }
 }
@@ -778,7 +781,13 @@ static FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
   const int px0 = std::max(plo[0], 0), px1 = std::min(phi[0], nx - 1);
   const int py0 = std::max(plo[1], 0), py1 = std::min(phi[1], ny - 1);
   p.split = (op == OP_AB) && (long long)nx * ny * nz >= kSplitNodes && px1 >= px0 && py1 >= py0;
-  if (!p.split) return p;
+  if (!p.split) {
+    if (op == OP_AB) {  // whole-grid launch of the A/B operators: 16 x 16 tiles
+      p.TXT = (nx + TileG::TXS - 1) / TileG::TXS;
+      p.TYT = (ny + TileG::TYS - 1) / TileG::TYS;
+    }
+    return p;
+  }
   p.RW = cdiv_i(px1 - px0 + 1, TX);
   p.RH = cdiv_i(py1 - py0 + 1, TY);
   TileMap& f = p.frame;
