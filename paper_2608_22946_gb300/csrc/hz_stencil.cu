@@ -21,8 +21,8 @@
 // shared memory a handful of times instead of 27.  Large grids are applied in
 // two launches: 32 x 8 tiles over the PML-free rectangle (3-partial shell
 // rows) and 64 x 4 / 4 x 64 tiles over the PML frame around it (tensor-product
-// rows, x-only / y-only / general); small grids in one launch choosing per
-// 32 x 8 tile.  Epilogues fuse the residual (with its norm), the two-sweep
+// rows, x-only / y-only / general); small grids in one launch of 16 x 16
+// tiles choosing the row form per tile.  Epilogues fuse the residual (with its norm), the two-sweep
 // Jacobi map from zero (Eq. jacobi-map, n_J = 2) and one further Jacobi sweep.
 //
 // The adjoint kernel applies (H^H x)_i = sum_delta conj(H_{i+delta}(-delta)) x_{i+delta};
@@ -188,9 +188,9 @@ __device__ __forceinline__ void table_a1a4(const R* __restrict__ tab, int nseg, 
   a4 = c[12] + u * (c[13] + u * (c[14] + u * c[15]));
 }
 
-// Which tiles a launch covers.  Rectangle launches (PATH 0 and 2, 32 x 8
-// tiles): tile (t, blockIdx.y) has its origin at (ox + 32 t, oy + 8 blockIdx.y)
-// and writes the columns up to (rx1, ry1).  Frame launches (PATH 1): the PML
+// Which tiles a launch covers.  Rectangle launches (PATH 0: 32 x 8 tiles,
+// PATH 2: 16 x 16): tile (t, blockIdx.y) has its origin at (ox + TXS t,
+// oy + TYS blockIdx.y) and writes the columns up to (rx1, ry1).  Frame launches (PATH 1): the PML
 // frame around the PML-free rectangle [px0, px1] x [py0, py1], as rows of
 // 64 x 4 tiles below and above it (full x range) followed by rows of 4 x 64
 // tiles left and right of it (its y range).  The blocks of all the launches of
@@ -762,7 +762,7 @@ struct FwdPlan {
   int zb = 4, nzb = 1;     // whole grid or PML-free rectangle
   int zbf = 4, nzbf = 1;   // PML frame
   bool split = false;
-  int TXT = 1, TYT = 1;  // whole-grid 32 x 8 tiling
+  int TXT = 1, TYT = 1;  // whole-grid tiling (16 x 16 for A/B, 32 x 8 for Q)
   int RW = 0, RH = 0;    // 32 x 8 tiling of the PML-free rectangle
   TileMap frame;         // frame tiling (count = frame tiles per z-block)
   long long blocks() const {
