@@ -53,6 +53,11 @@ def test_workspace_bytes_and_validation(lib):
         hz.workspace_bytes(48, 6, 1 / 36, 1.0)   # n_pml not divisible by 4
     with pytest.raises(hz.HzError):
         hz.workspace_bytes(48, 8, 1 / 32, 1.0, params=hz.default_params(m_4h=9))
+    with pytest.raises(hz.HzError) as e:
+        hz.workspace_bytes(0, 0, 1.0, 1.0)       # empty grid
+    assert e.value.status == hz.HZ_EINVAL
+    with pytest.raises(hz.HzError):
+        hz.workspace_bytes(16, 8, 1.0, 1.0)      # PML layers leave no physical domain
     big = hz.workspace_bytes(960, 24, 1 / 912, 1.0, max_nrhs=1)
     assert 150e9 < big < 280e9  # the 961^3 workload fits one GB300 with one source in flight
 

@@ -239,6 +239,19 @@ def test_sources_in_chunks_and_on_the_boundary(hz):
     s.close()
 
 
+def test_nonfinite_velocity_is_reported(hz):
+    """A NaN in the velocity model surfaces as HZ_ENONFINITE from the solve (the
+    residual norms are checked on the host), not as a silent NaN solution."""
+    w = W.homogeneous(n=24, n_pml=4)
+    c = w.c.copy()
+    c[5, 7, 9] = np.nan
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, c, params=hz.default_params(tol=1e-6), max_nrhs=1)
+    with pytest.raises(hz.HzError) as e:
+        s.helmholtz_solve(w.sources)
+    assert e.value.status == hz.HZ_ENONFINITE
+    s.close()
+
+
 def test_zero_source_amplitude_gives_zero(hz):
     w = W.homogeneous(n=24, n_pml=4)
     prob, s = make_pair(hz, w)
