@@ -76,7 +76,7 @@ typedef struct {
 } hz_source;
 
 /* Solver configuration; hz_default_params() fills Table 4 of the paper
- * (tol 1e-4 there; BASELINE workloads use 1e-6). */
+ * (tol 1e-4 there; the mixed-versus-FP64 study uses 1e-6). */
 typedef struct {
   double tol;          /* stop when ||A v - b|| / ||b|| <= tol (Eq. relative-residual) */
   int max_pc;          /* cap on preconditioner calls (outer FGMRES steps) */

@@ -5,9 +5,9 @@ periodic grid built from the stencil and transfer definitions; the vertex
 argument of the smoothing factor against dense sampling; the minimax linear
 program against the closed form for a disk.  The paper's admissibility claims
 for its fixed parameters (sigma, omega_2h, omega_4h) = (0.9, 0.8, 0.2) are
-checked with this build's tables; its printed diagnostic values depend on its
-own (unpublished) tables and are compared, not pinned, except the bottom-grid
-origin separation.
+checked with the fitted IOFD tables the solver uses; its printed diagnostic
+values depend on its own (unpublished) tables and are compared, not pinned,
+except the bottom-grid origin separation.
 """
 import itertools
 import math
@@ -121,7 +121,7 @@ def test_selected_parameters_are_admissible():
 
 def test_bottom_origin_separation_matches_paper():
     """delta_4h at (0.9, 0.2) (Sec. 4.4 prints 0.100): set by the low-frequency end
-    of the bottom symbol, it agrees with this build's tables to within 2 %."""
+    of the bottom symbol, it agrees with the fitted IOFD tables to within 2 %."""
     nu = np.linspace(*lfa.NU_RANGE, 73)
     th = lfa.sorted_angles(17, math.pi)
     NU, TH = np.meshgrid(nu, np.arange(len(th)), indexing="ij")
