@@ -327,6 +327,58 @@ def test_gmres_cycle_is_krylov_minimiser():
         assert np.allclose(x.ravel(), x0.ravel() + Zs @ y, atol=1e-9 * np.abs(x).max())
 
 
+def _transfer_matrices_1d(m):
+    """Full weighting (1/4, 1/2, 1/4) and linear interpolation between m + 1 fine
+    and m/2 + 1 coarse nodes, written from the stencil weights (zero outside)."""
+    mc = m // 2
+    R1 = np.zeros((mc + 1, m + 1))
+    P1 = np.zeros((m + 1, mc + 1))
+    for J in range(mc + 1):
+        R1[J, 2 * J] = 0.5
+        P1[2 * J, J] = 1.0
+        if 2 * J + 1 <= m:
+            R1[J, 2 * J + 1] = 0.25
+            P1[2 * J + 1, J] = 0.5
+            P1[2 * J + 1, J + 1] = 0.5
+        if J >= 1:
+            R1[J, 2 * J - 1] = 0.25
+    return R1, P1
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_shifted_vcycle_is_two_grid_error_operator(adjoint):
+    """With an exact 4h solve in place of C_4h, the shifted cycle of Eq.
+    shifted-auxiliary-cycle has the textbook two-grid error propagation
+    e - V(B e) = S^nJ (I - P B_4h^-1 R B_2h) S^nJ e, S = I - omega D^-1 B_2h,
+    on the shifted operators (Eq. shifted-operator) of a PML problem with
+    variable kh.  The matrices come from the Kronecker assembly and the
+    1-D transfer weights, not from the oracle's matrix-free code; swapping the
+    smoothing order, a stale residual before the post-sweeps, the unshifted
+    operator or a wrong transfer weight each break it.  The adjoint hierarchy
+    uses B^H and conj(D) throughout."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    p = tg.Params()
+    B2 = iofd.assemble(prob, 1, p.sigma).toarray()
+    B4 = iofd.assemble(prob, 2, p.sigma).toarray()
+    if adjoint:
+        B2, B4 = B2.conj().T, B4.conj().T
+    R1, P1 = _transfer_matrices_1d(prob.levels[1].n[0])
+    R = np.kron(np.kron(R1, R1), R1)
+    P = np.kron(np.kron(P1, P1), P1)
+    D = np.diag(B2)
+    S = np.eye(len(D)) - p.w_2h * B2 / D[:, None]
+    Sn = np.linalg.matrix_power(S, p.nJ_2h)
+    E = Sn @ (np.eye(len(D)) - P @ np.linalg.solve(B4, R @ B2)) @ Sn
+
+    M = tg.ThreeGrid(prob, p, adjoint=adjoint)
+    shape4 = prob.levels[2].shape
+    M.C_4h = lambda g: np.linalg.solve(B4, g.ravel()).reshape(shape4)
+    e = W.random_complex(prob.levels[1].shape, 31)
+    got = e - M.V_2h((B2 @ e.ravel()).reshape(e.shape))
+    ref = E @ e.ravel()
+    assert np.linalg.norm(got.ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
