@@ -379,6 +379,40 @@ def test_shifted_vcycle_is_two_grid_error_operator(adjoint):
     assert np.linalg.norm(got.ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_algorithm1_step_order_is_two_grid_error_operator(adjoint):
+    """Algorithm 1 with its two Krylov solves replaced by linear maps -- S_h(g,
+    x0) = x0 + omega D^-1 (g - A_h x0), K_2h = exact A_2h solve -- has the error
+    propagation e - M(A_h e) = S (I - P A_2h^-1 R A_h) S e, S = I - omega D^-1
+    A_h: steps 1-5 compose pre-smoothing from zero, restriction of the updated
+    residual, the 2h correction and post-smoothing from the corrected iterate.
+    Sparse matrices from the Kronecker assembly and the 1-D transfer weights."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    p = tg.Params()
+    A = iofd.assemble(prob, 0).tocsc()
+    A2 = iofd.assemble(prob, 1).tocsc()
+    if adjoint:
+        A, A2 = A.conj().T.tocsc(), A2.conj().T.tocsc()
+    R1, P1 = _transfer_matrices_1d(prob.levels[0].n[0])
+    R1, P1 = sp.csr_matrix(R1), sp.csr_matrix(P1)
+    R = sp.kron(sp.kron(R1, R1), R1, format="csr")
+    P = sp.kron(sp.kron(P1, P1), P1, format="csr")
+    d = A.diagonal()
+    om = p.w_h
+    S = lambda v: v - om * (A @ v) / d
+
+    M = tg.ThreeGrid(prob, p, adjoint=adjoint)
+    shape, shape2 = prob.levels[0].shape, prob.levels[1].shape
+    M.S_h = lambda g, x0: (np.zeros_like(g) if x0 is None else x0) + om * (
+        g - (A @ (np.zeros(g.size) if x0 is None else x0.ravel())).reshape(shape)) / d.reshape(shape)
+    M.K_2h = lambda r2: spla.spsolve(A2, r2.ravel()).reshape(shape2)
+    e = W.random_complex(shape, 32).ravel()
+    got = e - M((A @ e).reshape(shape)).ravel()
+    ref = S(e)
+    ref = S(ref - P @ spla.spsolve(A2, R @ (A @ ref)))
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
