@@ -413,6 +413,34 @@ def test_algorithm1_step_order_is_two_grid_error_operator(adjoint):
     assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_krylov_solves_use_unshifted_operators(adjoint):
+    """S_h (step 1) and K_2h (Eq. unshifted-middle-solve) iterate on the
+    unshifted A_h and A_2h: with an exact inverse of that operator as the
+    preconditioner, one Krylov step returns the exact solution.  Running either
+    on the shifted B or on the wrong level leaves a residual."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    p = tg.Params()
+    A = iofd.assemble(prob, 0).tocsc()
+    A2 = iofd.assemble(prob, 1).tocsc()
+    if adjoint:
+        A, A2 = A.conj().T.tocsc(), A2.conj().T.tocsc()
+    shape, shape2 = prob.levels[0].shape, prob.levels[1].shape
+    M = tg.ThreeGrid(prob, p, adjoint=adjoint)
+    M.J = lambda H, g, omega, nJ: spla.spsolve(A, g.ravel()).reshape(shape)
+    M.V_2h = lambda q: spla.spsolve(A2, q.ravel()).reshape(shape2)
+    g = W.random_complex(shape, 33)
+    x0 = W.random_complex(shape, 34)
+    ref = spla.spsolve(A, g.ravel())
+    for start in (None, x0):
+        got = M.S_h(g, start).ravel()
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    r2 = W.random_complex(shape2, 35)
+    ref2 = spla.spsolve(A2, r2.ravel())
+    got2 = M.K_2h(r2).ravel()
+    assert np.linalg.norm(got2 - ref2) <= 1e-10 * np.linalg.norm(ref2)
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
