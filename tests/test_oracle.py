@@ -441,6 +441,23 @@ def test_krylov_solves_use_unshifted_operators(adjoint):
     assert np.linalg.norm(got2 - ref2) <= 1e-10 * np.linalg.norm(ref2)
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_bottom_solve_uses_shifted_operator(adjoint):
+    """C_4h iterates on the shifted B_4h = L - (1 + i sigma) M at spacing 4h:
+    with an exact inverse of B_4h as its Jacobi stand-in, one step is exact."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    p = tg.Params()
+    B4 = iofd.assemble(prob, 2, p.sigma).tocsc()
+    if adjoint:
+        B4 = B4.conj().T.tocsc()
+    shape4 = prob.levels[2].shape
+    M = tg.ThreeGrid(prob, p, adjoint=adjoint)
+    M.J = lambda H, g, omega, nJ: spla.spsolve(B4, g.ravel()).reshape(shape4)
+    g = W.random_complex(shape4, 36)
+    ref = spla.spsolve(B4, g.ravel())
+    assert np.linalg.norm(M.C_4h(g).ravel() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
