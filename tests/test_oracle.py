@@ -158,6 +158,38 @@ def test_textbook_limit_is_7point_laplacian():
     assert np.allclose(Q(x), x)
 
 
+def test_q_operator_shells_and_constants():
+    """Q_h of Eq. q-operator with an arbitrary beta table: the four shell
+    weights times the shell sizes 1, 6, 12, 8 add up to one, so Q maps a
+    constant to itself at every node whose 27 neighbours are inside; on a plane
+    wave it multiplies by the shell-sum symbol Q_0 + 2 Q_1 sum cos + 4 Q_2 sum
+    cos cos + 8 Q_3 prod cos.  A weight on the wrong shell or a wrong
+    denominator breaks one of the two."""
+    w, prob0 = small_problem(n=16, n_pml=4, kind="random")
+    rng = np.random.default_rng(41)
+    T0 = prob0.tables
+    beta = rng.uniform(-0.5, 1.5, T0.beta.shape)
+    dbeta = rng.uniform(-1.0, 1.0, T0.dbeta.shape)
+    T = iofd.Tables(T0.s, T0.alpha, T0.dalpha, beta, dbeta)
+    prob = iofd.make_problem(w.c, w.n_pml, w.h, w.omega, w.gamma_max, T)
+    Q = iofd.operator_Q(prob)
+    shape = prob.levels[0].shape
+    one = Q(np.ones(shape, np.complex128))
+    assert np.allclose(one[1:-1, 1:-1, 1:-1], 1.0, rtol=0, atol=1e-13)
+    Z, Y, X = np.meshgrid(*[np.arange(m) for m in shape], indexing="ij")
+    lev = prob.levels[0]
+    for k in range(4):
+        th = rng.uniform(-math.pi, math.pi, 3)
+        pw = np.exp(1j * (th[0] * Z + th[1] * Y + th[2] * X))
+        c = tuple(rng.integers(1, m - 1) for m in shape)
+        b, _ = iofd.hermite(T.s, T.beta, T.dbeta, lev.eta_star[c])
+        q = [b[0], b[1] / 6, b[2] / 12, (1 - b[0] - b[1] - b[2]) / 8]
+        z = np.cos(th)
+        sym = (q[0] + 2 * q[1] * z.sum() + 4 * q[2] * (z[0] * z[1] + z[0] * z[2] + z[1] * z[2])
+               + 8 * q[3] * z.prod())
+        assert abs(Q(pw)[c] / pw[c] - sym) < 1e-12 * max(1.0, abs(sym))
+
+
 @pytest.mark.parametrize("L,sigma", [(0, 0.0), (1, 0.0), (1, 0.9), (2, 0.9)])
 def test_matrix_free_equals_kronecker_assembly(L, sigma):
     """Matrix-free rows (inside and outside the PML, variable kh) equal the
