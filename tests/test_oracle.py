@@ -490,6 +490,50 @@ def test_bottom_solve_uses_shifted_operator(adjoint):
     assert np.linalg.norm(M.C_4h(g).ravel() - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def _dense_fgmres_minimiser(A, M, r0, k):
+    """Residual-minimising correction over span{M r0, M (A M) r0, ...} (k
+    directions), by dense least squares on the explicit Krylov basis."""
+    K = [r0]
+    for _ in range(k - 1):
+        K.append(A(M(K[-1])))
+    Zs = np.stack([M(v).ravel() for v in K], axis=1)
+    AZ = np.stack([A(M(v)).ravel() for v in K], axis=1)
+    y = np.linalg.lstsq(AZ, r0.ravel(), rcond=None)[0]
+    return (Zs @ y).reshape(r0.shape), np.linalg.norm(r0.ravel() - AZ @ y)
+
+
+def test_outer_fgmres_counts_and_restarts():
+    """Outer FGMRES(m_out) (Eq. relative-residual stopping test, one
+    preconditioner call per Arnoldi step): a run capped at one cycle returns the
+    dense Krylov minimiser; a second cycle restarts from it; a tolerance met
+    inside a cycle stops at the first step whose minimal residual meets it; an
+    exact preconditioner needs one call."""
+    w, prob = small_problem(n=12, n_pml=4, kind="random")
+    A = iofd.operator_A(prob)
+    M = lambda v: tg.jacobi(A, v, 0.5, 2)
+    b = W.random_complex(prob.levels[0].shape, 37)
+    bn = np.linalg.norm(b)
+    m = 5
+    d1, res1 = _dense_fgmres_minimiser(A, M, b, m)
+    x, info = tg.fgmres_solve(A, M, b, tg.Params(tol=1e-30, max_pc=m, m_out=m))
+    assert info.pc_calls == m and len(info.history) == 2
+    assert np.linalg.norm((x - d1).ravel()) <= 1e-9 * np.linalg.norm(d1)
+    assert info.rel_res == pytest.approx(res1 / bn, rel=1e-9)
+    d2, res2 = _dense_fgmres_minimiser(A, M, b - A(d1), m)
+    x, info = tg.fgmres_solve(A, M, b, tg.Params(tol=1e-30, max_pc=2 * m, m_out=m))
+    assert info.pc_calls == 2 * m and len(info.history) == 3
+    assert np.linalg.norm((x - d1 - d2).ravel()) <= 1e-8 * np.linalg.norm(d1 + d2)
+    mins = [_dense_fgmres_minimiser(A, M, b, k)[1] / bn for k in range(1, m + 1)]
+    assert all(mins[k + 1] < mins[k] for k in range(m - 1))
+    tol = float(np.sqrt(mins[1] * mins[2]))          # met first at step 3
+    x, info = tg.fgmres_solve(A, M, b, tg.Params(tol=tol, max_pc=50, m_out=m))
+    assert info.pc_calls == 3 and info.rel_res == pytest.approx(mins[2], rel=1e-8)
+    Asp = iofd.assemble(prob).tocsc()
+    exact = lambda v: spla.spsolve(Asp, v.ravel()).reshape(v.shape)
+    x, info = tg.fgmres_solve(A, exact, b, tg.Params(tol=1e-10, max_pc=50, m_out=m))
+    assert info.pc_calls == 1 and info.rel_res <= 1e-10
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
