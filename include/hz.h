@@ -141,6 +141,23 @@ hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int m
 /* Replace the solver parameters (e.g. tolerance); cached CUDA graphs are dropped. */
 hz_status hz_set_params(hz_handle* h, const hz_params* params);
 
+/* Host-only check of the forward stencil's launch layout; no GPU work and no
+ * counterpart in the paper.  Replays, for level `level` of `grid` (the same
+ * checks as hz_create), how one forward application of op (HZ_OP_A, HZ_OP_B,
+ * or HZ_OP_Q on level 0) with nrhs right-hand sides and the given z-blocks
+ * (0: the built-in heuristic; zblock_f: the PML-frame launch, 0 = zblock)
+ * assigns grid nodes to CUDA blocks and threads.
+ *   counts_host  HOST, N_L bytes, or NULL: times each node of right-hand side 0
+ *                is written (saturating at 255; 1 everywhere is an exact cover).
+ *   blocks       HOST, or NULL: blocks per right-hand side (the fused
+ *                reductions keep one partial sum per block).
+ *   violations   HOST: tiles whose threads would write outside the grid, use a
+ *                row form that omits PML terms present at a written node, or
+ *                repeat / overrun a block id.  0 for a valid layout.
+ * Returns HZ_EINVAL for bad arguments (message in hz_last_error(NULL)). */
+hz_status hz_layout_check(const hz_grid* grid, int level, int op, int nrhs, int zblock, int zblock_f,
+                          unsigned char* counts_host, long long* blocks, long long* violations);
+
 /* Per-level coefficients, for inspection (Eq. iofd-clamped-coordinate,
  * Eq. iofd-shell-coefficients).
  *   kappa_dev  DEVICE double, N_L values: kappa_{L,i} = k(x_i) 2^L h.

@@ -24,7 +24,7 @@ _STATUS = {0: "HZ_OK", 1: "HZ_EINVAL", 2: "HZ_ENOMEM", 3: "HZ_ECUDA", 4: "HZ_ENO
 
 EXPORTED = ["hz_default_params", "hz_create", "hz_destroy", "hz_last_error", "hz_workspace_bytes",
             "hz_set_params", "iofd_coeffs", "iofd_apply", "threegrid_precond", "helmholtz_solve",
-            "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static"]
+            "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static", "hz_layout_check"]
 
 
 class HzGrid(ctypes.Structure):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.iofd_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.iofd_residual_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                          ctypes.c_int, vp]
+    lib.hz_layout_check.argtypes = [P(HzGrid), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, vp, P(ctypes.c_longlong), P(ctypes.c_longlong)]
     lib.threegrid_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
     lib.helmholtz_solve.argtypes = [vp, P(HzSource), ctypes.c_int, vp, vp, P(HzStats)]
     lib.helmholtz_adjoint_grad.argtypes = [vp, P(HzSource), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
@@ -284,3 +286,20 @@ def workspace_bytes(n, n_pml, h, omega, params=None, max_nrhs=1, gamma_max=1.119
     if st != HZ_OK:
         raise HzError(st, lib.hz_last_error(None).decode())
     return out.value
+
+
+def layout_check(n, n_pml, level=0, op=HZ_OP_A, nrhs=1, zblock=0, zblock_f=0, gamma_max=1.119058):
+    """hz_layout_check: per-node write counts (right-hand side 0, shape
+    (nz+1, ny+1, nx+1) of the level), blocks per right-hand side and the number
+    of layout violations of one forward stencil application.  Host only."""
+    lib = load_library()
+    nx, ny, nz = (n, n, n) if np.isscalar(n) else n
+    g = HzGrid(nx, ny, nz, n_pml, 1.0, 1.0, gamma_max)
+    f = 1 << level
+    counts = np.zeros((nz // f + 1, ny // f + 1, nx // f + 1), dtype=np.uint8)
+    blocks, bad = ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib.hz_layout_check(ctypes.byref(g), level, op, nrhs, zblock, zblock_f,
+                             counts.ctypes.data_as(ctypes.c_void_p), ctypes.byref(blocks), ctypes.byref(bad))
+    if st != HZ_OK:
+        raise HzError(st, lib.hz_last_error(None).decode())
+    return counts, blocks.value, bad.value

@@ -1100,6 +1100,26 @@ hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int m
   return st;
 }
 
+hz_status hz_layout_check(const hz_grid* grid, int level, int op, int nrhs, int zblock, int zblock_f,
+                          unsigned char* counts_host, long long* blocks, long long* violations) {
+  if (!grid || !violations) return HZ_EINVAL;
+  hz_handle tmp;
+  hz_status st = run_guarded(&tmp, [&] {
+    check_grid(*grid);
+    HZ_REQUIRE(level >= 0 && level <= 2, "level must be 0, 1 or 2");
+    HZ_REQUIRE(op == HZ_OP_A || op == HZ_OP_B || op == HZ_OP_Q, "op must be HZ_OP_A, HZ_OP_B or HZ_OP_Q");
+    HZ_REQUIRE(op != HZ_OP_Q || level == 0, "Q_h is defined on the fine level only");
+    HZ_REQUIRE(nrhs >= 1 && zblock >= 0 && zblock_f >= 0, "nrhs must be >= 1, z-blocks >= 0");
+    Level lv;
+    level_dims(*grid, level, lv);
+    if (counts_host) std::memset(counts_host, 0, (size_t)lv.N);
+    *violations = replay_fwd_layout(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, op == HZ_OP_Q ? OP_Q : OP_AB,
+                                    nrhs, zblock, zblock_f, counts_host, blocks);
+  });
+  g_create_error = tmp.err;
+  return st;
+}
+
 hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* params, const double* table_host,
                     int table_rows, int max_nrhs, void* stream, hz_handle** out) {
   if (!out) return HZ_EINVAL;

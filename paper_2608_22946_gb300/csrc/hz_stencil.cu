@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <cstdio>
+#include <vector>
 
 #include "hz_kernels.h"
 
@@ -210,7 +211,7 @@ struct FrameTile {
   bool wide;
 };
 
-__device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int t) {
+__host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int t) {
   FrameTile f;
   const int nw = m.nwx * (m.nw_lo + m.nw_hi);
   if (t < nw) {
@@ -913,6 +914,85 @@ long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, co
   const int zb = zblock > 0 ? zblock : choose_zblock(nx, ny, nz, nrhs);
   const FwdPlan p = plan_layout(nx, ny, nz, plain_lo, plain_hi, OP_AB, zb, zblock_f);
   return p.blocks();
+}
+
+// Host replay of launch_fwd_t and k_fwd's block and thread decode (the plan,
+// the frame tile decode, the thread-to-column map, the z-block of every CTA,
+// the row form each tile takes and its block id for fused reductions).
+// Violations counted: a written column outside the grid, a column outside the
+// PML-free range on a row form that drops that axis's PML terms (form 0 both
+// axes, form 1 y, form 3 x), a block id out of range or repeated.  counts
+// (nx * ny * nz bytes, or null) receives how often each node of right-hand
+// side 0 is written, saturating at 255.
+long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs, int zblock,
+                            int zblock_f, unsigned char* counts, long long* blocks) {
+  const int zb = zblock > 0 ? zblock : choose_zblock(nx, ny, nz, nrhs);
+  const FwdPlan p = plan_layout(nx, ny, nz, plo, phi, op, zb, zblock_f);
+  const long long nblk = p.blocks();
+  if (blocks) *blocks = nblk;
+  std::vector<unsigned char> seen((size_t)nblk, 0);
+  long long bad = 0;
+  const bool ab = op == OP_AB;
+  auto plain_x = [&](int x) { return x >= plo[0] && x <= phi[0]; };
+  auto plain_y = [&](int y) { return y >= plo[1] && y <= phi[1]; };
+  auto cta = [&](int TXS, int x0, int y0, int rx1, int ry1, int form, int zbk, int bz, long long bid) {
+    if (bid < 0 || bid >= nblk || seen[(size_t)bid]++) ++bad;
+    const int zb0 = bz * zbk, zb1 = std::min(zb0 + zbk, nz);
+    for (int tid = 0; tid < NT; ++tid) {
+      const int gx = x0 + tid % TXS, gy = y0 + tid / TXS;
+      if (!(gx <= rx1 && gy <= ry1)) continue;  // inactive thread
+      if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) {
+        ++bad;
+        continue;
+      }
+      if (ab && ((form == 0 && !(plain_x(gx) && plain_y(gy))) || (form == 1 && !plain_y(gy)) ||
+                 (form == 3 && !plain_x(gx))))
+        ++bad;
+      if (counts)
+        for (int z = zb0; z < zb1; ++z) {
+          unsigned char& c = counts[((size_t)z * ny + gy) * nx + gx];
+          if (c < 255) ++c;
+        }
+    }
+  };
+  if (!p.split) {
+    const int TXS = ab ? TileG::TXS : TileSq::TXS, TYS = ab ? TileG::TYS : TileSq::TYS;
+    for (int bz = 0; bz < p.nzb; ++bz)
+      for (int by = 0; by < p.TYT; ++by)
+        for (int bx = 0; bx < p.TXT * nrhs; ++bx) {
+          if (bx % nrhs) continue;  // right-hand side 0
+          const int t = bx / nrhs, x0 = t * TXS, y0 = by * TYS;
+          const bool plain = x0 >= plo[0] && x0 + TXS - 1 <= phi[0] && y0 >= plo[1] && y0 + TYS - 1 <= phi[1];
+          cta(TXS, x0, y0, nx - 1, ny - 1, (!ab || plain) ? 0 : 2, p.zb, bz, t + (long long)p.TXT * (by + p.TYT * bz));
+        }
+  } else {
+    const int px0 = p.frame.px0, py0 = p.frame.py0;
+    for (int bz = 0; bz < p.nzb; ++bz)
+      for (int by = 0; by < p.RH; ++by)
+        for (int bx = 0; bx < p.RW * nrhs; ++bx) {
+          if (bx % nrhs) continue;
+          const int t = bx / nrhs;
+          cta(TileSq::TXS, px0 + t * TileSq::TXS, py0 + by * TileSq::TYS, p.frame.px1, p.frame.py1, 0, p.zb, bz,
+              t + (long long)p.RW * (by + p.RH * bz));
+        }
+    const long long off = (long long)p.RW * p.RH * p.nzb;
+    for (int bz = 0; bz < p.nzbf; ++bz)
+      for (int bx = 0; bx < p.frame.count * nrhs; ++bx) {
+        if (bx % nrhs) continue;
+        const int t = bx / nrhs;
+        const FrameTile f = decode_frame(p.frame, t);
+        const long long bid = off + t + (long long)p.frame.count * bz;
+        if (f.wide) {
+          const bool xplain = f.x0 >= plo[0] && f.x0 + TileW::TXS - 1 <= phi[0];
+          cta(TileW::TXS, f.x0, f.y0, f.rx1, f.ry1, xplain ? 3 : 2, p.zbf, bz, bid);
+        } else {
+          cta(TileT::TXS, f.x0, f.y0, f.rx1, f.ry1, 1, p.zbf, bz, bid);
+        }
+      }
+  }
+  for (unsigned char v : seen)
+    if (v != 1) ++bad;
+  return bad;
 }
 
 template <class R, int MODE, int OP>

@@ -65,3 +65,55 @@ def test_workspace_bytes_and_validation(lib):
 def test_null_handle_is_rejected(lib):
     assert lib.iofd_apply(None, 0, 0, 0, None, None, 1, None) == 1
     assert lib.hz_destroy(None) == 1
+
+
+def _layout_cases():
+    """Grids on both sides of the two-launch threshold (2^20 nodes): ragged
+    PML-free rectangles (widths not multiples of the 32 x 8 tile), thin, thick
+    and absent PML, non-cubic shapes, every level, Q, several right-hand sides
+    and z-blocks forced to the tuner's extremes."""
+    cases = []
+    for n in range(8, 133, 4):
+        for p in (0, 4, 8, 12, 16, 24):
+            if 2 * p < n:
+                cases.append(((n, n, n), p, 0, 0, 1, 0, 0))
+    for shape, p in [((104, 104, 104), 16), ((288, 288, 12), 4), ((300, 116, 40), 8), ((40, 300, 116), 12),
+                     ((116, 40, 300), 16), ((252, 252, 56), 24), ((160, 132, 56), 4), ((128, 128, 64), 0)]:
+        for lev in (0, 1, 2):
+            for op in (0, 1, 2):
+                if op == 2 and lev:
+                    continue
+                for nrhs, zb, zbf in [(1, 0, 0), (3, 4, 64), (2, 64, 4), (1, 7, 22)]:
+                    cases.append((shape, p, lev, op, nrhs, zb, zbf))
+    return cases
+
+
+def test_forward_launch_layout_is_an_exact_cover(lib):
+    """Every node of a forward stencil application is written exactly once
+    (so the PML-free rectangle launch and the PML-frame launch, which run
+    concurrently on two streams, write disjoint nodes), no thread writes outside
+    the grid, each tile's row form drops only PML terms that are zero at its
+    written nodes, and the blocks' reduction ids are a permutation of
+    0 .. blocks-1 (the size of the per-block partial-sum array)."""
+    import numpy as np
+    import paper_2608_22946_gb300 as hz
+    split_seen = 0
+    for shape, p, lev, op, nrhs, zb, zbf in _layout_cases():
+        counts, blocks, bad = hz.layout_check(shape, p, level=lev, op=op, nrhs=nrhs, zblock=zb, zblock_f=zbf)
+        key = (shape, p, lev, op, nrhs, zb, zbf)
+        assert bad == 0, key
+        assert counts.min() == 1 and counts.max() == 1, (key, np.argwhere(counts != 1)[:3])
+        assert blocks >= 1
+        split_seen += counts.size >= (1 << 20) and op != 2 and p > 0
+    assert split_seen >= 10
+
+
+def test_layout_check_validates_arguments(lib):
+    import paper_2608_22946_gb300 as hz
+    for kw in [dict(level=3), dict(op=hz.HZ_OP_A_ADJ), dict(op=hz.HZ_OP_Q, level=1), dict(nrhs=0),
+               dict(zblock=-1)]:
+        with pytest.raises(hz.HzError) as e:
+            hz.layout_check(48, 8, **kw)
+        assert e.value.status == hz.HZ_EINVAL
+    with pytest.raises(hz.HzError):
+        hz.layout_check(50, 8)      # intervals not divisible by 4
