@@ -16,7 +16,11 @@ Sec. 4.3-4.4, evaluated with the same IOFD tables as the solver:
 * ``bottom_multiplier``: lambda_4h of Eq. bottom-radius-indicator;
 * ``ideal_polynomial_factor``: the degree-m minimax factor of Eq.
   bottom-ideal-gmres-factor by the supporting-half-plane linear program the
-  paper describes (64 directions), returning the attained maximum.
+  paper describes (64 directions), returning the attained maximum;
+* ``threegrid_block``: the 64 x 64 Fourier block of Algorithm 1 over the
+  harmonics of Eq. three-grid-harmonics with every Krylov map replaced by a
+  prescribed polynomial (closing paragraph of Sec. 4.4; no value printed
+  there).
 
 Sampling sets follow the paper's symmetry reduction (sign changes and
 coordinate permutations leave every quantity unchanged): angles in
@@ -149,6 +153,93 @@ def ideal_polynomial_factor(lam, degree, n_dirs=64):
     c = res.x[:degree] + 1j * res.x[degree:2 * degree]
     p = 1.0 + powers @ c
     return float(res.x[-1]), float(np.max(np.abs(p))), c
+
+
+# ----------------------------------------------------------------------------
+# the full h - 2h - 4h hierarchy (closing paragraph of Sec. 4.4)
+# ----------------------------------------------------------------------------
+def harmonics64(theta):
+    """q in {0,1,2,3}^3 (itertools.product order) and the fine-grid angles
+    theta + (pi/2) q of Eq. three-grid-harmonics, theta in (-pi/4, pi/4]^3."""
+    qs = np.array(list(itertools.product(range(4), repeat=3)))
+    return qs, np.asarray(theta, dtype=np.float64)[None, :] + 0.5 * math.pi * qs
+
+
+def neumann_coefficients(m):
+    """Coefficients c_0..c_{m-1} of the fixed m-step map x = M sum_j c_j (H M)^j g
+    whose residual polynomial is (1 - z)^m (m Richardson steps); one
+    right-hand-side-independent choice for the prescribed polynomials."""
+    return np.array([math.comb(m, j + 1) * (-1) ** j for j in range(m)], dtype=np.float64)
+
+
+def _jacobi_block(b, d, omega, n_sweeps):
+    """n sweeps of damped Jacobi from zero on one harmonic space: the diagonal
+    omega/d sum_{k<n} (1 - omega b/d)^k (Eq. lfa-jacobi-symbol), as a matrix."""
+    s = 1.0 - omega * b / d
+    return np.diag(omega / d * sum(s ** k for k in range(n_sweeps)))
+
+
+def _polynomial_map(H, M, coeffs):
+    """g -> M sum_j c_j (H M)^j g: a right-preconditioned Krylov map from zero
+    with its coefficients prescribed (closing paragraph of Sec. 4.4)."""
+    HM = H @ M
+    acc = np.zeros_like(HM)
+    power = np.eye(len(H), dtype=HM.dtype)
+    for c in coeffs:
+        acc = acc + c * power
+        power = HM @ power
+    return M @ acc
+
+
+def threegrid_block(tables, nu, theta, sigma=0.9, omega=(0.8, 0.8, 0.2), n_sweeps=(2, 2, 2), m=(2, 10, 4),
+                    c_2h=2, coeffs=None):
+    """64 x 64 Fourier block of the preconditioner M_h of Algorithm 1 on the
+    harmonics of Eq. three-grid-harmonics, every Krylov map replaced by a
+    prescribed polynomial (S_h: m_h steps, each 2h FGMRES cycle: m_2h steps,
+    C_4h: m_4h steps; `coeffs` = (c_h, c_2h, c_4h), default Neumann).
+
+    Levels: A_h, A_2h unshifted, B_2h, B_4h shifted (Eq. shifted-iofd-levels),
+    symbols in units of h^-2; the fine harmonic theta_q aliases on the 2h grid
+    to 2 theta + pi (q mod 2), every 2h harmonic on the 4h grid to 4 theta;
+    transfers between aliases carry prod (1 + cos)/2 of the finer angle (Eq.
+    lfa-transfer-symbol), full weighting the adjoint column.  Returns M with
+    the fine symbol a (so that I - M diag(a) is the error propagation)."""
+    ch, c2, c4 = coeffs or (neumann_coefficients(m[0]), neumann_coefficients(m[1]), neumann_coefficients(m[2]))
+    qs, th = harmonics64(theta)
+    rs = np.array(list(itertools.product((0, 1), repeat=3)))
+    r_index = (qs % 2) @ np.array([4, 2, 1])                   # alias of theta_q among the 8 2h harmonics
+    th2 = 2.0 * np.asarray(theta, dtype=np.float64)[None, :] + math.pi * rs
+    th4 = 4.0 * np.asarray(theta, dtype=np.float64)
+    Ch = shell_coefficients(tables, kappa_of(1, nu), 0.0)
+    A2c = shell_coefficients(tables, kappa_of(2, nu), 0.0)
+    B2c = shell_coefficients(tables, kappa_of(2, nu), sigma)
+    B4c = shell_coefficients(tables, kappa_of(4, nu), sigma)
+    a_h = symbol(Ch, th)
+    a_2 = symbol(A2c, th2) / 4.0
+    b_2 = symbol(B2c, th2) / 4.0
+    b_4 = np.atleast_1d(symbol(B4c, th4) / 16.0)
+    rho = lambda ang: np.prod((1.0 + np.cos(ang)) / 2.0, axis=-1)
+    P1 = np.zeros((64, 8), dtype=np.complex128)
+    P1[np.arange(64), r_index] = rho(th)
+    P2 = rho(th2).astype(np.complex128)[:, None]                # (8, 1)
+    R1, R2 = P1.T, P2.T
+    Ah, A2, B2, B4 = np.diag(a_h), np.diag(a_2), np.diag(b_2), np.diag(b_4)
+    Jh = _jacobi_block(a_h, Ch[0], omega[0], n_sweeps[0])
+    J2 = _jacobi_block(b_2, B2c[0] / 4.0, omega[1], n_sweeps[1])
+    J4 = _jacobi_block(b_4, B4c[0] / 16.0, omega[2], n_sweeps[2])
+    I8, I64 = np.eye(8), np.eye(64)
+    C4 = _polynomial_map(B4, J4, c4)                            # bottom solve C_4h
+    Y = J2                                                      # shifted cycle V_2h^sigma
+    Yt = Y + P2 @ C4 @ R2 @ (I8 - B2 @ Y)
+    V = Yt + J2 @ (I8 - B2 @ Yt)
+    G2 = _polynomial_map(A2, V, c2)                             # K_2h: c_2h cycles from zero
+    K = np.zeros((8, 8), dtype=np.complex128)
+    for _ in range(c_2h):
+        K = K + G2 @ (I8 - A2 @ K)
+    Gh = _polynomial_map(Ah, Jh, ch)                            # S_h(g; x0) = x0 + Gh (g - A x0)
+    Zpre = Gh                                                   # Algorithm 1, steps 1-5
+    Zt = Zpre + P1 @ K @ R1 @ (I64 - Ah @ Zpre)
+    return Zt + Gh @ (I64 - Ah @ Zt), a_h
 
 
 def report(tables=None, n_low=28, n_full=33, n_nu=145, n_nu_poly=25, n_poly=12):

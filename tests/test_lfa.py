@@ -1,7 +1,8 @@
 """Local Fourier analysis of the hierarchy (paper Sec. 4), oracle side.
 
-The harmonic blocks are pinned against a brute-force two-grid cycle on a
-periodic grid built from the stencil and transfer definitions; the vertex
+The harmonic blocks (8 x 8 two-grid, 64 x 64 three-grid) are pinned against
+brute-force cycles on periodic grids built from the stencil and transfer
+definitions; the vertex
 argument of the smoothing factor against dense sampling; the minimax linear
 program against the closed form for a disk.  The paper's admissibility claims
 for its fixed parameters (sigma, omega_2h, omega_4h) = (0.9, 0.8, 0.2) are
@@ -127,3 +128,67 @@ def test_bottom_origin_separation_matches_paper():
     NU, TH = np.meshgrid(nu, np.arange(len(th)), indexing="ij")
     lam = lfa.bottom_multiplier(T, NU.ravel(), th[TH.ravel()], 0.9, 0.2, 2)
     assert abs(np.abs(lam).min() - 0.100) <= 0.002
+
+
+def _dense_poly_map(H, M, coeffs):
+    """g -> M sum_j c_j (H M)^j g as a dense matrix."""
+    out = np.zeros_like(H)
+    power = np.eye(len(H), dtype=np.complex128)
+    for c in coeffs:
+        out = out + c * power
+        power = H @ M @ power
+    return M @ out
+
+
+def _dense_jacobi(H, omega, n):
+    d = np.diag(H)
+    S = np.eye(len(H)) - omega * H / d[:, None]
+    out = np.zeros_like(H)
+    power = np.eye(len(H), dtype=np.complex128)
+    for _ in range(n):
+        out = out + power
+        power = S @ power
+    return out @ np.diag(omega / d)
+
+
+@pytest.mark.parametrize("nu,coeff_kind", [(7.0, "neumann"), (13.0, "random")])
+def test_threegrid_block_matches_periodic_hierarchy(nu, coeff_kind):
+    """The 64 x 64 block of Algorithm 1 with prescribed polynomials equals the
+    dense linear map of the same algorithm on periodic 8^3 / 4^3 / 2^3 grids
+    (stencils from the shell coefficients, damped Jacobi on the diagonal,
+    trilinear prolongation and full weighting), restricted to the 64
+    harmonics theta + (pi/2) q of every grid-compatible theta."""
+    sigma, om, nJ, m, c2h = 0.9, (0.8, 0.8, 0.2), (2, 2, 2), (2, 3, 4), 2
+    if coeff_kind == "neumann":
+        coeffs = tuple(lfa.neumann_coefficients(k) for k in m)
+    else:
+        rng = np.random.default_rng(3)
+        coeffs = tuple(rng.normal(size=k) + 1j * rng.normal(size=k) for k in m)
+    Ah = _periodic_operator(lfa.shell_coefficients(T, lfa.kappa_of(1, nu), 0.0), 8, 1.0)
+    A2 = _periodic_operator(lfa.shell_coefficients(T, lfa.kappa_of(2, nu), 0.0), 4, 1.0 / 4.0)
+    B2 = _periodic_operator(lfa.shell_coefficients(T, lfa.kappa_of(2, nu), sigma), 4, 1.0 / 4.0)
+    B4 = _periodic_operator(lfa.shell_coefficients(T, lfa.kappa_of(4, nu), sigma), 2, 1.0 / 16.0)
+    P1, R1 = _periodic_transfers(4)
+    P2, R2 = _periodic_transfers(2)
+    Jh, J2, J4 = _dense_jacobi(Ah, om[0], nJ[0]), _dense_jacobi(B2, om[1], nJ[1]), _dense_jacobi(B4, om[2], nJ[2])
+    C4 = _dense_poly_map(B4, J4, coeffs[2])
+    I2, Ih = np.eye(64), np.eye(512)
+    Yt = J2 + P2 @ C4 @ R2 @ (I2 - B2 @ J2)
+    V = Yt + J2 @ (I2 - B2 @ Yt)
+    G2 = _dense_poly_map(A2, V, coeffs[1])
+    K = np.zeros((64, 64), dtype=np.complex128)
+    for _ in range(c2h):
+        K = K + G2 @ (I2 - A2 @ K)
+    Gh = _dense_poly_map(Ah, Jh, coeffs[0])
+    Zt = Gh + P1 @ K @ R1 @ (Ih - Ah @ Gh)
+    M = Zt + Gh @ (Ih - Ah @ Zt)
+    grid = np.stack(np.meshgrid(*(np.arange(8),) * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    for k in itertools.product((0, 1), repeat=3):
+        theta = 2 * math.pi * np.array(k) / 8.0                     # in (-pi/4, pi/4]^3
+        _, th = lfa.harmonics64(theta)
+        Phi = np.exp(1j * grid @ th.T)                              # (512, 64)
+        ref = (Phi.conj().T @ M @ Phi) / 512.0
+        got, a = lfa.threegrid_block(T, nu, theta, sigma, om, nJ, m, c2h, coeffs)
+        assert np.allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max()), (k, np.abs(got - ref).max())
+        # the fine symbol is the diagonal of A_h on these modes
+        assert np.allclose(a, np.diag(Phi.conj().T @ Ah @ Phi) / 512.0, atol=1e-10 * np.abs(a).max())
