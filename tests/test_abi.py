@@ -117,3 +117,33 @@ def test_layout_check_validates_arguments(lib):
         assert e.value.status == hz.HZ_EINVAL
     with pytest.raises(hz.HzError):
         hz.layout_check(50, 8)      # intervals not divisible by 4
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: loading a library that is not there raises."""
+    import paper_2608_22946_gb300 as hz
+    monkeypatch.setattr(hz, "_lib", None)
+    with pytest.raises(RuntimeError, match="build the CUDA library"):
+        hz.load_library(str(tmp_path / "libhz.so"))
+
+
+def test_solver_requires_a_gpu(lib):
+    """Without a CUDA device the solver refuses to run instead of computing on the host."""
+    import numpy as np
+    import torch
+    import paper_2608_22946_gb300 as hz
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="CUDA device is required"):
+        hz.Solver(16, 4, 1 / 8, 2.0, np.ones((17, 17, 17)))
+
+
+def test_package_does_not_use_the_oracle():
+    """The product package neither imports nor reads anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_2608_22946_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
+                assert not re.search(r"\boracle[./]\w", src), f
