@@ -1,6 +1,6 @@
-"""Host-side test of the multi-process path of bench.py: two gloo ranks on the
-CPU run the same barrier / max-over-ranks / aggregation helpers that the GPU
-replicas use with NCCL (replicas share nothing else)."""
+"""Host-side tests of bench.py: two gloo ranks on the CPU run the same
+barrier / max-over-ranks / aggregation helpers that the GPU replicas use with
+NCCL (replicas share nothing else); the clock record's parsing."""
 import os
 import socket
 
@@ -53,3 +53,24 @@ def test_single_process_defaults(monkeypatch):
     assert (w, r, pg) == (1, 0, None)
     assert bench.allreduce_max(pg, 3.0) == 3.0
     assert bench.aggregate_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_clock_summary_parses_samples_and_reasons():
+    """The clock record attached to every bench line: median SM clock under
+    load, the maximum, and every throttle reason seen Active at least once
+    (nvidia-smi csv, noheader, nounits)."""
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 950.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 950.3, 0x0, Not Active, Not Active, Not Active, Not Active",   # unreadable sample
+        "garbage",
+    ]
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs.lines = ["0, 1500, 2070, 700, 0x48, Active, Not Active, Active, Not Active"]
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    cs.lines = []
+    assert cs.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
