@@ -635,6 +635,32 @@ def test_phase_audit_of_tables():
 
 
 # ---------------------------------------------------------------- gradient
+def test_row_derivatives_match_central_differences():
+    """d A_i(delta)/d m_i and d Q_i(delta)/d m_i (every offset, inside and
+    outside the PML; the PML nodes carry the copied physical value) against
+    central differences of the row coefficients under a node-wise random
+    perturbation of m = 1/c^2: each row depends on its own node only."""
+    n, p = 12, 4
+    w = W.random_field(n=n, n_pml=p, nsrc=1, nrec_side=4)
+    prob0 = iofd.make_problem(w.c, p, w.h, w.omega, w.gamma_max)
+    m0 = 1.0 / prob0.c_ext ** 2
+    xi = np.random.default_rng(4).uniform(0.5, 1.5, m0.shape)
+    eps = 1e-5
+    probs = [iofd.make_problem(1.0 / np.sqrt(m0 * (1 + sgn * eps * xi)), p, w.h, w.omega, w.gamma_max)
+             for sgn in (1, -1)]
+    dm = 1.0 / probs[0].c_ext ** 2 - 1.0 / probs[1].c_ext ** 2
+    assert np.all(np.abs(dm) > 0)
+    for d in iofd.OFFSETS:
+        fd = (iofd.row_coefficient(probs[0].levels[0], probs[0].tables, d)
+              - iofd.row_coefficient(probs[1].levels[0], probs[1].tables, d)) / dm
+        ref = og.row_coefficient_dm(prob0, m0, d)
+        assert np.abs(fd - ref).max() <= 1e-6 * np.abs(ref).max(), d
+        fq = (iofd.q_coefficient(probs[0].levels[0], probs[0].tables, d)
+              - iofd.q_coefficient(probs[1].levels[0], probs[1].tables, d)) / dm
+        refq = og.q_coefficient_dm(prob0, m0, d)
+        assert np.abs(fq - refq).max() <= 1e-6 * np.abs(refq).max() + 1e-12, d
+
+
 def test_gradient_matches_central_differences():
     """Adjoint-state dJ/dm against central differences of J(m) on random voxels
     (including one next to the PML, whose extension copies fold onto it)."""
