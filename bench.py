@@ -14,6 +14,9 @@ node through one outer FGMRES step with its three-grid preconditioner call),
 summed over ranks.  Replicas (N > 1) solve independent copies: no collective
 on the data path ("scaling": "weak").
 
+Other workloads: --workload homogeneous_48 | layered_inclusion_224x16 (16
+sources batched); --stencil-only times the fine-grid A_h apply alone.
+
 --impl reference times the CPU oracle (the plain complex128 implementation
 of the paper's method) on a bounded sample of the same workload.
 """
@@ -37,6 +40,36 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+# Workloads by name: hz_workloads generator, whether all of its sources form
+# one batch, and the "data" description of the JSON line.  The numeric
+# aliases 1-3 of --config name the same workloads.
+WORKLOADS = {
+    "gaussian_lens_288": ("gaussian_lens", False, "seeded Gaussian-lens velocity, point source"),
+    "homogeneous_48": ("homogeneous", False, "constant velocity, centre point source"),
+    "layered_inclusion_224x16": ("layered_inclusion", True,
+                                 "seeded five-layer medium with a fast sphere, 16 point sources"),
+}
+CONFIG_ALIAS = {"1": "homogeneous_48", "2": "gaussian_lens_288", "3": "layered_inclusion_224x16"}
+L2_BYTES = 129e6
+
+
+def resolve_workload(name):
+    """(workload, sources solved per step, nrhs, data description) of a named workload."""
+    import hz_workloads as W
+    gen, batched, desc = WORKLOADS[name]
+    w = getattr(W, gen)()
+    sources = list(w.sources) if batched else list(w.sources[:1])
+    return w, sources, len(sources), desc
+
+
+def l2_note(n_nodes, nrhs):
+    """How the timed inputs relate to the 129 MB L2 (the step is not re-flushed)."""
+    mb = 8.0 * n_nodes * nrhs / 1e6
+    if 8.0 * n_nodes * nrhs > L2_BYTES:
+        return f"inputs larger than L2 (each fine complex64 field set {mb:.0f} MB)"
+    return f"inputs smaller than L2 ({mb:.1f} MB per fine complex64 field set): L2-resident timing"
 
 
 _T0 = time.perf_counter()
@@ -182,12 +215,13 @@ def run_reference(args):
     # the oracle runs on the host of rank 0 only; other ranks exit at once
     if int(os.environ.get("RANK", "0")) != 0:
         return
+    gen = WORKLOADS[args.workload][0]
     for _ in range(args.warmup):
-        oracle_sample("gaussian_lens")
+        oracle_sample(gen)
     vals = []
     t_all = time.perf_counter()
     for _ in range(max(1, args.steps)):
-        v, dt, cores, desc = oracle_sample("gaussian_lens")
+        v, dt, cores, desc = oracle_sample(gen)
         vals.append((v, dt))
     t_all = time.perf_counter() - t_all
     value = statistics.median([v for v, _ in vals])
@@ -195,7 +229,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GUpdates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "gaussian_lens_288", "sample": f"gaussian_lens_{ORACLE_SAMPLE_N}"},
+            "config": {"workload": args.workload, "sample": f"{gen}_{ORACLE_SAMPLE_N}"},
             "cpu_baseline": {"value": value, "unit": "GUpdates/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "GUpdates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -209,19 +243,12 @@ def run_gpu(args):
     import numpy as np
     import torch
 
-    import hz_workloads as W
     import paper_2608_22946_gb300 as hz
 
     world, rank, local, pg = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
-    w = {"2": W.gaussian_lens, "1": W.homogeneous, "3": W.layered_inclusion}[args.config]()
-    if args.config == "3":
-        sources = w.sources
-        nrhs = len(sources)
-    else:
-        sources = w.sources[:1]
-        nrhs = 1
+    w, sources, nrhs, data_desc = resolve_workload(args.workload)
     params = hz.default_params(tol=1e-6, precision=hz.HZ_C64)
     noconv = False
     if args.max_pc:
@@ -266,13 +293,12 @@ def run_gpu(args):
     result = {"metric": METRIC, "value": value, "unit": "GUpdates/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-              "data": "synthetic (seeded Gaussian-lens velocity, point source)",
-              "config": {"workload": {"2": "gaussian_lens_288", "1": "homogeneous_48",
-                                      "3": "layered_inclusion_224x16"}[args.config],
+              "data": f"synthetic ({data_desc})",
+              "config": {"workload": args.workload,
                          "grid_intervals": w.n, "n_pml": w.n_pml, "fine_nodes": N, "nrhs": nrhs,
                          "ppw": 6, "tol": 1e-6, "precision": "c64 hierarchy, FP64 outer scalars + refinement",
                          "parallelism": f"replicas x{world}",
-                         "l2": "inputs larger than L2 (each fine complex64 vector 193 MB)"},
+                         "l2": l2_note(N, nrhs)},
               "time_to_solution_s": t_step, "pc_calls": pc, "rel_res": rel,
               "refine_passes": stats[-1]["refine_passes"], "t_setup_s": stats[-1]["t_setup"],
               "zblock_tuned": {"rectangle": stats[-1].get("zblock"), "frame": stats[-1].get("zblock_frame")},
@@ -365,9 +391,8 @@ def run_stencil_only(args):
     """Time the fine-grid complex64 A_h apply alone (the kernel the roofline
     line reports), K launches after 3 warm-ups, inputs larger than L2."""
     import torch
-    import hz_workloads as W
     import paper_2608_22946_gb300 as hz
-    w = {"2": W.gaussian_lens, "1": W.homogeneous, "3": W.layered_inclusion}[args.config]()
+    w, _, _, _ = resolve_workload(args.workload)
     s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=1)
     x = torch.randn((1,) + s.shape, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
@@ -451,7 +476,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="2", choices=["1", "2", "3"])
+    ap.add_argument("--workload", default="gaussian_lens_288", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=None, choices=sorted(CONFIG_ALIAS), help=argparse.SUPPRESS)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -464,6 +490,8 @@ def main():
     ap.add_argument("--tols", default="1e-4", help="comma-separated tolerances for --paper-media")
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"], help="for --paper-media")
     args = ap.parse_args()
+    if args.config:
+        args.workload = CONFIG_ALIAS[args.config]
     if args.paper_media:
         run_paper_media(args)
     elif args.stencil_only:

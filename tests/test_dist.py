@@ -74,3 +74,37 @@ def test_clock_summary_parses_samples_and_reasons():
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     cs.lines = []
     assert cs.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_named_workloads_and_l2_note():
+    """Each named bench workload builds with its stated grid and batch; the
+    numeric aliases name the same workloads; the L2 note matches the sizes."""
+    import bench
+    for name, (n, nrhs) in {"homogeneous_48": (48, 1), "gaussian_lens_288": (288, 1),
+                            "layered_inclusion_224x16": (224, 16)}.items():
+        w, sources, k, desc = bench.resolve_workload(name)
+        assert (w.n, k, len(sources)) == (n, nrhs, nrhs) and desc
+        assert name.startswith(w.name)
+    assert set(bench.CONFIG_ALIAS.values()) == set(bench.WORKLOADS)
+    assert bench.l2_note(289 ** 3, 1).startswith("inputs larger than L2 (each fine complex64 field set 193 MB")
+    assert bench.l2_note(49 ** 3, 1).startswith("inputs smaller than L2")
+
+
+def test_reference_arm_line(tmp_path):
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON
+    line with the contract's keys, for the workload selected by name or alias."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--config", "1"], capture_output=True, text=True, timeout=600,
+                         env=dict(os.environ, RANK="0"))
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"]:
+        assert k in line, k
+    assert line["impl"] == "reference" and line["config"]["workload"] == "homogeneous_48"
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
