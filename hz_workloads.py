@@ -6,8 +6,8 @@ velocity models, source and receiver positions.  It contains none of the
 method's arithmetic (no stencil, no PML profile, no IOFD coefficient, no
 Krylov step), so that the oracle and the CUDA path stay independent.
 
-Conventions (paper Sec. 5, "mesh dimensions report the number of fine-grid
-intervals ... an n^3 mesh has (n+1)^3 nodal unknowns"):
+Conventions (paper Sec. 5: a mesh is named by its fine-grid interval count
+n per direction, and every one of its (n+1)^3 nodes is an unknown):
 
 * ``n`` intervals per direction including ``n_pml`` PML layers on each side;
   nodes ``i = 0..n``; physical box ``[0,1]^3`` spans ``n - 2 n_pml`` intervals,

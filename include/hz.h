@@ -9,8 +9,8 @@
  *
  * Conventions shared by every entry point
  *   - Grid: nx, ny, nz intervals per axis INCLUDING n_pml PML layers on each
- *     side; (nx+1)(ny+1)(nz+1) nodal unknowns (Sec. 5, "an n^3 mesh has
- *     (n+1)^3 nodal unknowns").  nx, ny, nz and n_pml must be divisible by 4
+ *     side; every one of the (nx+1)(ny+1)(nz+1) nodes is an unknown
+ *     (Sec. 5 counts meshes this way).  nx, ny, nz and n_pml must be divisible by 4
  *     (two coarsenings, each halving the PML layers, Sec. 3.1).
  *   - Field layout: x fastest, then y, then z; for nrhs right-hand sides the
  *     fields are stacked, [rhs][z][y][x].  Complex values are interleaved

@@ -7,8 +7,8 @@ indexed [iz, iy, ix]; nodes outside 0..n carry the Dirichlet value u = 0
 * PML distance d_j is counted in nodes from the first physical node and
   clamped to L_pml, so the ghost node just outside the box has gamma_max;
   it only enters through the half-node stretch xi_{-1/2}, xi_{n+1/2}.
-* Coarse levels use n/2^L intervals and n_pml/2^L PML layers (Sec. 3.1:
-  "the number of PML layers is halved"), velocity injected from fine node
+* Coarse levels use n/2^L intervals and n_pml/2^L PML layers (Sec. 3.1
+  halves the layer count with each coarsening), velocity injected from fine node
   2^L j, and gamma evaluated at the coarse node's own position.
 * Q_h uses its shell form everywhere, inside the PML too (Sec. 2.2 gives
   only the shell form).
@@ -28,8 +28,8 @@ ETA_MAX = 0.4   # Eq. iofd-clamped-coordinate
 
 
 # ----------------------------------------------------------------------------
-# IOFD tables and cubic Hermite interpolation (Sec. 2.2: "alpha_j ... are cubic
-# Hermite interpolants of optimized tabulated values")
+# IOFD tables and cubic Hermite interpolation (Sec. 2.2: each alpha_j and
+# beta_j is a piecewise cubic Hermite curve through tabulated node values)
 # ----------------------------------------------------------------------------
 @dataclasses.dataclass
 class Tables:

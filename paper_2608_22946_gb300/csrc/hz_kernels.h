@@ -135,8 +135,9 @@ void launch_add_c64_to_c128_scaled(const cx<float>* d, cx<double>* x, const doub
 template <class R>
 void launch_norm2(const cx<R>* v, int n, int nrhs, const Reduce& red, cudaStream_t s);
 
-// Set-up: kappa_L[j] = omega * ell / c_ext[2^L j] with c extended into the PML
-// by its nearest physical value (Sec. 2.1, Sec. 3.1).
+// Set-up: kappa_L[j] = omega * ell / c_ext[2^L j], where c_ext is c inside the
+// physical box and, at a PML node, c at the closest physical node (Sec. 2.1,
+// Sec. 3.1).
 template <class R>
 void launch_setup_kappa(const double* c, int nxf, int nyf, int nzf, int n_pml, int stride, double omega,
                         double ell, R* kappa, cudaStream_t s);
