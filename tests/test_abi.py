@@ -147,3 +147,20 @@ def test_package_does_not_use_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
                 assert not re.search(r"\boracle[./]\w", src), f
+
+
+def test_reduction_slots_are_sized_by_the_smallest_zblock(lib):
+    """The fused-norm partial-sum array is sized from the block count at the
+    smallest z-block (4 planes for both launches); no z-block the heuristic or
+    the autotuner can choose (4 .. 64, frame and rectangle independently)
+    yields more blocks."""
+    import paper_2608_22946_gb300 as hz
+    for shape, p in [((288, 288, 288), 16), ((224, 224, 224), 16), ((152, 152, 152), 12), ((104, 104, 104), 16),
+                     ((300, 116, 40), 8), ((48, 48, 48), 8)]:
+        for lev in (0, 1, 2):
+            for nrhs in (1, 16):
+                _, worst, _ = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=4, zblock_f=4)
+                for zb in (0, 5, 6, 8, 12, 22, 46, 64):
+                    for zbf in (0, 4, 8, 22, 64):
+                        _, b, bad = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=zb, zblock_f=zbf)
+                        assert bad == 0 and b <= worst, (shape, lev, nrhs, zb, zbf, b, worst)
