@@ -534,6 +534,33 @@ def test_outer_fgmres_counts_and_restarts():
     assert info.pc_calls == 1 and info.rel_res <= 1e-10
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_s_step_bottom_solve_equals_gmres(adjoint):
+    """Reading of C_4h (Sec. 3.2): m_4h = 4 CA-GMRES steps -- monomial basis
+    p_0 = g / ||g||, p_{k+1} = B J(p_k), the least-squares problem
+    min || ||g|| p_0 - [p_1..p_4] y || solved through the 5 x 5 Gram block and
+    its Cholesky factor, x = sum_k y_k J(p_k) -- give the iterate of
+    GMRES(4) right-preconditioned by J on the same Krylov space, which the
+    oracle runs (on the shifted 4h operator of a PML problem)."""
+    w, prob = small_problem(n=16, n_pml=4, kind="random")
+    p = tg.Params()
+    M = tg.ThreeGrid(prob, p, adjoint=adjoint)
+    B = M.op(M.B_4h)
+    J = lambda v: M.J(M.B_4h, v, p.w_4h, p.nJ_4h)
+    g = W.random_complex(prob.levels[2].shape, 38)
+    beta = np.linalg.norm(g)
+    P = [g / beta]
+    for _ in range(p.m_4h):
+        P.append(B(J(P[-1])))
+    Pm = np.stack([v.ravel() for v in P], axis=1)
+    G = Pm.conj().T @ Pm                                   # Gram block (5 x 5)
+    L = np.linalg.cholesky(G[1:, 1:])
+    y = np.linalg.solve(L.conj().T, np.linalg.solve(L, beta * G[1:, 0]))
+    x_ca = sum(y[k] * J(P[k]) for k in range(p.m_4h))
+    x_gm = tg.fgmres_cycle(B, J, g, None, p.m_4h)
+    assert np.linalg.norm((x_ca - x_gm).ravel()) <= 1e-8 * np.linalg.norm(x_gm)
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
