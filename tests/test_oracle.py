@@ -561,6 +561,55 @@ def test_s_step_bottom_solve_equals_gmres(adjoint):
     assert np.linalg.norm((x_ca - x_gm).ravel()) <= 1e-8 * np.linalg.norm(x_gm)
 
 
+def test_cgs_selective_reorthogonalisation_and_givens_equal_mgs_lstsq():
+    """Reading of the orthogonalisation and small least-squares steps (the
+    paper names neither): classical Gram-Schmidt with a second pass only when
+    the first removes more than half of ||w||^2 (criterion of Daniel, Gragg,
+    Kaufman and Stewart), and Givens rotations on the Hessenberg matrix, give
+    the flexible GMRES iterate of the oracle's modified Gram-Schmidt and lstsq
+    (outer FGMRES(5) on A_h with a Jacobi preconditioner, from a nonzero x0)."""
+    w, prob = small_problem(n=12, n_pml=4, kind="random")
+    A = iofd.operator_A(prob)
+    Mj = lambda v: tg.jacobi(A, v, 0.8, 2)
+    g = W.random_complex(prob.levels[0].shape, 39)
+    x0 = 1e-2 * W.random_complex(prob.levels[0].shape, 40)
+    m = 5
+    r0 = (g - A(x0)).ravel()
+    beta = np.linalg.norm(r0)
+    V = [r0 / beta]
+    Z, H = [], np.zeros((m + 1, m), dtype=np.complex128)
+    for j in range(m):
+        z = Mj(V[j].reshape(g.shape)).ravel()
+        Z.append(z)
+        wv = A(z.reshape(g.shape)).ravel()
+        Vm = np.stack(V, axis=1)
+        h = Vm.conj().T @ wv
+        w1 = wv - Vm @ h
+        if np.vdot(w1, w1).real <= 0.5 * np.vdot(wv, wv).real:
+            h2 = Vm.conj().T @ w1
+            w1 = w1 - Vm @ h2
+            h = h + h2
+        H[:j + 1, j] = h
+        H[j + 1, j] = np.linalg.norm(w1)
+        V.append(w1 / H[j + 1, j])
+    # Givens rotations reduce H to upper triangular form; back substitution
+    R = H.copy()
+    rhs = np.zeros(m + 1, dtype=np.complex128)
+    rhs[0] = beta
+    for j in range(m):
+        a, b = R[j, j], R[j + 1, j]
+        rho = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+        c, s = a / rho, b / rho
+        G = np.array([[np.conj(c), np.conj(s)], [-s, c]])
+        R[j:j + 2, j:] = G @ R[j:j + 2, j:]
+        rhs[j:j + 2] = G @ rhs[j:j + 2]
+    y = np.linalg.solve(np.triu(R[:m, :m]), rhs[:m])
+    x = x0.ravel() + np.stack(Z, axis=1) @ y
+    ref = tg.fgmres_cycle(A, Mj, g, x0, m).ravel()
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert abs(abs(rhs[m]) - np.linalg.norm(g.ravel() - A(x.reshape(g.shape)).ravel())) <= 1e-8 * beta
+
+
 def test_cycle_with_zero_rhs_returns_zero():
     w, prob = small_problem(n=12, n_pml=4)
     A = iofd.operator_A(prob)
