@@ -237,12 +237,19 @@ def scaled(kind: str, n: int, n_pml: int, **kw) -> Workload:
     return f(n=n, n_pml=n_pml, **kw)
 
 
-def config(idx: int) -> Workload:
-    """The five workloads: 1 homogeneous 48^3, 2 Gaussian lens 288^3,
-    3 layered + inclusion 224^3 x16 sources, 4 random field 152^3 with
-    receivers, 5 geophysical 960^3 x4 sources."""
-    return {1: homogeneous, 2: gaussian_lens, 3: layered_inclusion,
-            4: random_field, 5: geophysical}[idx]()
+# The full-size workloads, named by medium, grid intervals and source count.
+WORKLOADS = {
+    "homogeneous_48": homogeneous,
+    "gaussian_lens_288": gaussian_lens,
+    "layered_inclusion_224x16": layered_inclusion,
+    "random_field_152x8": random_field,
+    "geophysical_960x4": geophysical,
+}
+
+
+def by_name(name: str) -> Workload:
+    """One of the full-size workloads at its default size and seed."""
+    return WORKLOADS[name]()
 
 
 def random_complex(shape, seed, dtype=np.complex128):

@@ -108,3 +108,23 @@ def test_reference_arm_line(tmp_path):
     assert line["impl"] == "reference" and line["config"]["workload"] == "homogeneous_48"
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_workload_names_used_by_the_tests_exist():
+    """Every workload the full-size GPU tests and the bench name resolves in
+    hz_workloads, to the generator of that medium at its default size."""
+    import re
+    import bench
+    import hz_workloads as W
+    here = os.path.dirname(os.path.abspath(__file__))
+    names = set()
+    for f in os.listdir(here):
+        if f.endswith(".py"):
+            src = open(os.path.join(here, f)).read()
+            names |= set(re.findall(r'by_name\("(\w+)"\)', src))
+            names |= set(re.findall(r'\("(\w+_\d+(?:x\d+)?)", \d+\)', src))
+    assert {"gaussian_lens_288", "geophysical_960x4", "layered_inclusion_224x16", "random_field_152x8"} <= names
+    assert names <= set(W.WORKLOADS) and set(bench.WORKLOADS) <= set(W.WORKLOADS)
+    for name in ("homogeneous_48", "random_field_152x8"):
+        w = W.by_name(name)
+        assert name.startswith(w.name) and w.n == int(re.search(r"_(\d+)", name).group(1))

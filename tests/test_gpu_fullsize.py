@@ -63,11 +63,11 @@ def oracle_rows_vs_gpu(prob_level, tables, x_dev, y_dev, pts, sigma=0.0):
     return np.max(np.abs(got - ref) / mag)
 
 
-@pytest.mark.parametrize("cfg", [2, 5])
-def test_full_size_apply_sampled_rows(hz, cfg):
+@pytest.mark.parametrize("name,seed", [("gaussian_lens_288", 2), ("geophysical_960x4", 5)])
+def test_full_size_apply_sampled_rows(hz, name, seed):
     """A_h (complex64) on the 289^3 Gaussian-lens and 961^3 geophysical grids:
     sampled rows within 1e-5 of the oracle's, relative to the row magnitude."""
-    w = W.config(cfg)
+    w = W.by_name(name)
     tables = iofd.load_tables()
     lev = iofd.make_level_points(w.c, w.n_pml, w.h, w.omega, w.gamma_max, 0)
     c_dev = torch.from_numpy(w.c).to("cuda", torch.float64)
@@ -76,7 +76,7 @@ def test_full_size_apply_sampled_rows(hz, cfg):
     gen = torch.Generator(device="cuda").manual_seed(11)
     x = torch.randn((1,) + s.shape, dtype=torch.complex64, device="cuda", generator=gen)
     y = s.iofd_apply(x, op=hz.HZ_OP_A, level=0)
-    rng = np.random.default_rng(cfg)
+    rng = np.random.default_rng(seed)
     err = oracle_rows_vs_gpu(lev, tables, x, y, sample_nodes(lev.shape, w.n_pml, rng))
     assert err <= 1e-5, err
     # shifted operator on the 2h level of the same grid
@@ -92,7 +92,7 @@ def test_full_size_solve_lens_288(hz):
     """The benchmark solve (complex64 hierarchy, FP64 refinement, 1e-6): the FP64
     residual of v, recomputed by the complex128 operator, is <= 1e-6, and
     sampled complex128 rows agree with the oracle's to 1e-12."""
-    w = W.config(2)
+    w = W.by_name("gaussian_lens_288")
     s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=hz.default_params(tol=1e-6), max_nrhs=1)
     v, u, st = s.helmholtz_solve(w.sources)
     assert st["rel_res"] <= 1e-6
@@ -148,7 +148,7 @@ def test_full_size_batched_layered_224x16(hz):
     """16 sources in one batched solve (224^3 layered medium with a 10x
     inclusion): every source converges to 1e-6 (FP64 residual recomputed), and
     source 0 matches its single-source solve."""
-    w = W.config(3)
+    w = W.by_name("layered_inclusion_224x16")
     nsrc = len(w.sources)
     s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=hz.default_params(tol=1e-6), max_nrhs=nsrc)
     v, _, st = s.helmholtz_solve(w.sources, want_u=False)
@@ -172,7 +172,7 @@ def test_full_size_gradient_random_152_fd(hz):
     receivers, 152^3 random medium) through torch.autograd against central
     finite differences of the misfit at 20 random interior voxels."""
     from paper_2608_22946_gb300.autograd import helmholtz_misfit
-    w = W.config(4)
+    w = W.by_name("random_field_152x8")
     params = hz.default_params(tol=1e-12, max_pc=2000, max_refine=20)
     nsrc = len(w.sources)
     # synthetic data from the perturbed model
