@@ -191,19 +191,9 @@ def _polynomial_map(H, M, coeffs):
     return M @ acc
 
 
-def threegrid_block(tables, nu, theta, sigma=0.9, omega=(0.8, 0.8, 0.2), n_sweeps=(2, 2, 2), m=(2, 10, 4),
-                    c_2h=2, coeffs=None):
-    """64 x 64 Fourier block of the preconditioner M_h of Algorithm 1 on the
-    harmonics of Eq. three-grid-harmonics, every Krylov map replaced by a
-    prescribed polynomial (S_h: m_h steps, each 2h FGMRES cycle: m_2h steps,
-    C_4h: m_4h steps; `coeffs` = (c_h, c_2h, c_4h), default Neumann).
-
-    Levels: A_h, A_2h unshifted, B_2h, B_4h shifted (Eq. shifted-iofd-levels),
-    symbols in units of h^-2; the fine harmonic theta_q aliases on the 2h grid
-    to 2 theta + pi (q mod 2), every 2h harmonic on the 4h grid to 4 theta;
-    transfers between aliases carry prod (1 + cos)/2 of the finer angle (Eq.
-    lfa-transfer-symbol), full weighting the adjoint column.  Returns M with
-    the fine symbol a (so that I - M diag(a) is the error propagation)."""
+def _threegrid_parts(tables, nu, theta, sigma, omega, n_sweeps, m, coeffs):
+    """Per-level blocks on the harmonics of theta: symbols (units h^-2),
+    transfers, Jacobi maps and the bottom-solve and V-cycle maps."""
     ch, c2, c4 = coeffs or (neumann_coefficients(m[0]), neumann_coefficients(m[1]), neumann_coefficients(m[2]))
     qs, th = harmonics64(theta)
     rs = np.array(list(itertools.product((0, 1), repeat=3)))
@@ -222,24 +212,43 @@ def threegrid_block(tables, nu, theta, sigma=0.9, omega=(0.8, 0.8, 0.2), n_sweep
     P1 = np.zeros((64, 8), dtype=np.complex128)
     P1[np.arange(64), r_index] = rho(th)
     P2 = rho(th2).astype(np.complex128)[:, None]                # (8, 1)
-    R1, R2 = P1.T, P2.T
-    Ah, A2, B2, B4 = np.diag(a_h), np.diag(a_2), np.diag(b_2), np.diag(b_4)
-    Jh = _jacobi_block(a_h, Ch[0], omega[0], n_sweeps[0])
+    B2, B4 = np.diag(b_2), np.diag(b_4)
     J2 = _jacobi_block(b_2, B2c[0] / 4.0, omega[1], n_sweeps[1])
     J4 = _jacobi_block(b_4, B4c[0] / 16.0, omega[2], n_sweeps[2])
-    I8, I64 = np.eye(8), np.eye(64)
+    I8 = np.eye(8)
     C4 = _polynomial_map(B4, J4, c4)                            # bottom solve C_4h
     Y = J2                                                      # shifted cycle V_2h^sigma
-    Yt = Y + P2 @ C4 @ R2 @ (I8 - B2 @ Y)
+    Yt = Y + P2 @ C4 @ P2.T @ (I8 - B2 @ Y)
     V = Yt + J2 @ (I8 - B2 @ Yt)
-    G2 = _polynomial_map(A2, V, c2)                             # K_2h: c_2h cycles from zero
+    return dict(a_h=a_h, Ah=np.diag(a_h), A2=np.diag(a_2), P1=P1, V=V, c2=c2, ch=ch,
+                Jh=_jacobi_block(a_h, Ch[0], omega[0], n_sweeps[0]))
+
+
+def threegrid_block(tables, nu, theta, sigma=0.9, omega=(0.8, 0.8, 0.2), n_sweeps=(2, 2, 2), m=(2, 10, 4),
+                    c_2h=2, coeffs=None):
+    """64 x 64 Fourier block of the preconditioner M_h of Algorithm 1 on the
+    harmonics of Eq. three-grid-harmonics, every Krylov map replaced by a
+    prescribed polynomial (S_h: m_h steps, each 2h FGMRES cycle: m_2h steps,
+    C_4h: m_4h steps; `coeffs` = (c_h, c_2h, c_4h), default Neumann).
+
+    Levels: A_h, A_2h unshifted, B_2h, B_4h shifted (Eq. shifted-iofd-levels),
+    symbols in units of h^-2; the fine harmonic theta_q aliases on the 2h grid
+    to 2 theta + pi (q mod 2), every 2h harmonic on the 4h grid to 4 theta;
+    transfers between aliases carry prod (1 + cos)/2 of the finer angle (Eq.
+    lfa-transfer-symbol), full weighting the adjoint column.  Returns M with
+    the fine symbol a (so that I - M diag(a) is the error propagation)."""
+    d = _threegrid_parts(tables, nu, theta, sigma, omega, n_sweeps, m, coeffs)
+    Ah, A2, P1, V = d["Ah"], d["A2"], d["P1"], d["V"]
+    R1 = P1.T
+    I8, I64 = np.eye(8), np.eye(64)
+    G2 = _polynomial_map(A2, V, d["c2"])                        # K_2h: c_2h cycles from zero
     K = np.zeros((8, 8), dtype=np.complex128)
     for _ in range(c_2h):
         K = K + G2 @ (I8 - A2 @ K)
-    Gh = _polynomial_map(Ah, Jh, ch)                            # S_h(g; x0) = x0 + Gh (g - A x0)
+    Gh = _polynomial_map(Ah, d["Jh"], d["ch"])                  # S_h(g; x0) = x0 + Gh (g - A x0)
     Zpre = Gh                                                   # Algorithm 1, steps 1-5
     Zt = Zpre + P1 @ K @ R1 @ (I64 - Ah @ Zpre)
-    return Zt + Gh @ (I64 - Ah @ Zt), a_h
+    return Zt + Gh @ (I64 - Ah @ Zt), d["a_h"]
 
 
 def report(tables=None, n_low=28, n_full=33, n_nu=145, n_nu_poly=25, n_poly=12):
@@ -267,6 +276,58 @@ def report(tables=None, n_low=28, n_full=33, n_nu=145, n_nu_poly=25, n_poly=12):
     return out
 
 
+def _spectral_sweep(tables, coeffs, n_theta, n_nu):
+    """sup |1 - lambda| and inf |lambda| of M_h A_h over theta in [0, pi/4]^3
+    (sorted representatives) and nu in [6, 24]."""
+    worst, sep = 0.0, np.inf
+    for nu in np.linspace(*NU_RANGE, n_nu):
+        for th in sorted_angles(n_theta, math.pi / 4):
+            M, a = threegrid_block(tables, nu, th, coeffs=coeffs)
+            lam = np.linalg.eigvals(M * a[None, :])
+            worst = max(worst, float(np.abs(1.0 - lam).max()))
+            sep = min(sep, float(np.abs(lam).min()))
+    return worst, sep
+
+
+def threegrid_report(tables=None, n_theta=7, n_nu=19):
+    """The linearised three-grid map at (sigma, omega_2h, omega_4h) = (0.9, 0.8,
+    0.2) and the Table 4 step counts, with two right-hand-side-independent
+    choices of the polynomials: Neumann (residual (1 - z)^m) at every level,
+    and minimax at every level -- the degree-4 bottom factor of the LP above,
+    then the degree-10 and degree-2 minimax factors over the sampled spectra of
+    A_2h V_2h and A_h J_h that the levels below produce."""
+    T = tables or iofd.load_tables()
+    out = {}
+    neumann = (neumann_coefficients(2), neumann_coefficients(10), neumann_coefficients(4))
+    out["neumann_sup_1_minus_lambda"], out["neumann_inf_lambda"] = _spectral_sweep(T, neumann, n_theta, n_nu)
+    thp = sorted_angles(12, math.pi)
+    NUp, THp = np.meshgrid(np.linspace(*NU_RANGE, 25), np.arange(len(thp)), indexing="ij")
+    _, _, c4 = ideal_polynomial_factor(bottom_multiplier(T, NUp.ravel(), thp[THp.ravel()], 0.9, 0.2, 2), 4)
+    # residual polynomial 1 + sum_k c_k z^k  <->  map coefficients q_j = -c_{j+1}
+    q4 = -c4
+    lam2, lamh = [], []
+    for nu in np.linspace(*NU_RANGE, 10):
+        for th in sorted_angles(5, math.pi / 4):
+            AV, AJ = _level_operators(T, nu, th, q4)
+            lam2.append(np.linalg.eigvals(AV))
+            lamh.append(AJ)
+    _, _, c2 = ideal_polynomial_factor(np.concatenate(lam2), 10)
+    _, _, ch = ideal_polynomial_factor(np.concatenate(lamh), 2)
+    out["minimax_sup_1_minus_lambda"], out["minimax_inf_lambda"] = _spectral_sweep(T, (-ch, -c2, q4), n_theta, n_nu)
+    return out
+
+
+def _level_operators(tables, nu, theta, q4, sigma=0.9, omega=(0.8, 0.8, 0.2), n_sweeps=(2, 2, 2)):
+    """A_2h V_2h (8 x 8, with the bottom map q4) and the diagonal of A_h J_h
+    (64 values) on the harmonics of theta: the operators whose spectra the
+    2h and h polynomials act on."""
+    d = _threegrid_parts(tables, nu, theta, sigma, omega, n_sweeps, (2, 10, 4),
+                         (neumann_coefficients(2), neumann_coefficients(10), q4))
+    return d["A2"] @ d["V"], d["a_h"] * np.diag(d["Jh"])
+
+
 if __name__ == "__main__":
-    for k, v in report().items():
-        print(f"{k:16s} {v:.4g}")
+    import sys
+    rep = threegrid_report() if "--threegrid" in sys.argv else report()
+    for k, v in rep.items():
+        print(f"{k:28s} {v:.4g}")

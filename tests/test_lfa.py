@@ -192,3 +192,14 @@ def test_threegrid_block_matches_periodic_hierarchy(nu, coeff_kind):
         assert np.allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max()), (k, np.abs(got - ref).max())
         # the fine symbol is the diagonal of A_h on these modes
         assert np.allclose(a, np.diag(Phi.conj().T @ Ah @ Phi) / 512.0, atol=1e-10 * np.abs(a).max())
+
+
+def test_fixed_polynomial_three_grid_map_does_not_contract():
+    """With right-hand-side-independent polynomials the linearised three-grid
+    map is no contraction over the sampled range: Neumann polynomials diverge,
+    and even minimax polynomials at every level leave sup |1 - lambda| at 1 --
+    the resonant 2h modes put eigenvalues of A_2h V_2h at the origin, where
+    every residual polynomial equals 1."""
+    r = lfa.threegrid_report(T, n_theta=3, n_nu=4)
+    assert r["neumann_sup_1_minus_lambda"] > 1e3
+    assert 1.0 - 1e-9 <= r["minimax_sup_1_minus_lambda"] < 1.01
