@@ -63,8 +63,27 @@ def test_workspace_bytes_and_validation(lib):
 
 
 def test_null_handle_is_rejected(lib):
+    """Every entry point that takes a handle or an output returns HZ_EINVAL
+    for a null one before any CUDA call; the launch counter reads without a GPU."""
+    import paper_2608_22946_gb300 as hz
+    p = hz.default_params()
     assert lib.iofd_apply(None, 0, 0, 0, None, None, 1, None) == 1
     assert lib.hz_destroy(None) == 1
+    assert lib.hz_set_params(None, ctypes.byref(p)) == 1
+    assert lib.iofd_coeffs(None, 0, None, None) == 1
+    assert lib.threegrid_precond(None, None, None, 1, 0, 0, None) == 1
+    assert lib.helmholtz_solve(None, None, 0, None, None, None) == 1
+    assert lib.helmholtz_adjoint_grad(None, None, 0, None, 0, None, None, None, None) == 1
+    assert lib.iofd_residual_static(None, 0, 0, 0, None, None, None, None, 1, None) == 1
+    assert lib.hz_workspace_bytes(None, ctypes.byref(p), 1, None) == 1
+    g = hz.HzGrid(48, 48, 48, 8, 1 / 32, 1.0, 1.1)
+    assert lib.hz_create(ctypes.byref(g), None, ctypes.byref(p), None, 17, 1, None, None) == 1
+    h = ctypes.c_void_p()
+    assert lib.hz_create(None, None, ctypes.byref(p), None, 17, 1, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert "null" in lib.hz_last_error(None).decode()
+    assert lib.hz_layout_check(None, 0, 0, 1, 0, 0, None, None, None) == 1
+    assert hz.kernel_launches() >= 0
 
 
 def _layout_cases():
