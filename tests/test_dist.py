@@ -128,3 +128,18 @@ def test_workload_names_used_by_the_tests_exist():
     for name in ("homogeneous_48", "random_field_152x8"):
         w = W.by_name(name)
         assert name.startswith(w.name) and w.n == int(re.search(r"_(\d+)", name).group(1))
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the oracle and prints; the other ranks
+    exit 0 at once without output."""
+    import subprocess
+    import sys
+    import time
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                         capture_output=True, text=True, timeout=300,
+                         env=dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
+    assert out.returncode == 0 and out.stdout.strip() == ""
+    assert time.perf_counter() - t0 < 60
