@@ -95,6 +95,82 @@ def test_velocity_extension_nearest_interior():
     assert ce[0, 0, 0] == c[4, 4, 4] and ce[16, 2, 9] == c[12, 4, 9]
 
 
+# ---------------------------------------------------------------- coarse levels
+def _same_level(la, lb):
+    """True when two levels define the same rows: intervals, PML layers,
+    spacing, kappa and the per-axis stretch factors at nodes and half nodes."""
+    return (tuple(la.n) == tuple(lb.n) and la.n_pml == lb.n_pml and la.ell == lb.ell
+            and np.array_equal(la.kappa, lb.kappa)
+            and all(np.array_equal(pa[0], pb[0]) and np.array_equal(pa[1], pb[1])
+                    for pa, pb in zip(la.pml, lb.pml)))
+
+
+def _coarse_case(shape=(40, 24, 32), n_pml=8, seed=3):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(1.5, 3.0, tuple(m + 1 for m in shape))   # values in the PML too
+    h, omega = 1.0 / (min(shape) - 2 * n_pml), 17.0
+    return c, n_pml, h, omega
+
+
+@pytest.mark.parametrize("L", [1, 2])
+def test_coarse_level_is_the_problem_rediscretised_on_the_coarse_grid(L):
+    """Sec. 3.1: level L is the same PML problem discretised on the grid of
+    spacing 2^L h -- the velocity (extended into the PML from the physical box)
+    sampled at the coarse nodes, i.e. fine node 2^L j; a PML of the same
+    physical thickness, i.e. n_pml / 2^L layers; kappa = omega 2^L h / c.  So
+    the oracle's level L must be level 0 of a problem built directly on the
+    coarse grid from the raw velocity at every 2^L-th fine node, with spacing
+    2^L h and n_pml / 2^L layers, at the same omega; and its operator rows the
+    same.  Independent spot values: kappa at one node from the velocity of the
+    fine node it sits on, and the stretch at a coarse PML node and half node
+    from gamma evaluated at their physical distance into the layer."""
+    c, p, h, omega = _coarse_case()
+    f = 1 << L
+    prob = iofd.make_problem(c, p, h, omega)
+    coarse = iofd.make_problem(c[::f, ::f, ::f], p // f, f * h, omega, nlevels=1)
+    lev = prob.levels[L]
+    assert _same_level(lev, coarse.levels[0])
+    x = W.random_complex(lev.shape, 11)
+    for sigma in (0.0, 0.9):
+        assert np.array_equal(iofd.operator_A(prob, L, sigma)(x), iofd.operator_A(coarse, 0, sigma)(x))
+    # kappa at coarse node (iz, iy, ix): the fine node (f iz, f iy, f ix), moved to
+    # the nearest physical node when it lies in the PML
+    n = tuple(m - 1 for m in c.shape)
+    for j in [(0, 1, 2), (2, 3, 1), (lev.shape[0] - 1, 1, lev.shape[2] - 2)]:
+        fine = [min(max(f * jj, p), nn - p) for jj, nn in zip(j, n)]
+        assert lev.kappa[j] == pytest.approx(omega * (f * h) / c[tuple(fine)], rel=1e-15)
+    # stretch at coarse node 1 of the x axis and at the half node between nodes
+    # 0 and 1: gamma from the physical distance into the layer of thickness p h
+    gm, L_pml = prob.gamma_max, p * h
+    gamma = lambda x_pos: gm * (1 - math.cos(math.pi * max(L_pml - x_pos, 0.0) / (2 * L_pml)))
+    xin, xih = lev.pml[2]
+    assert abs(xin[1] - 1 / (1 + 1j * gamma(1 * f * h))) < 1e-14
+    assert abs(xih[1] - 1 / (1 + 0.5j * (gamma(0.0) + gamma(f * h)))) < 1e-14
+
+
+def test_coarse_level_pin_rejects_planted_mistakes():
+    """The comparison above is sharp: levels built with kappa = omega h / c
+    (spacing not scaled), with the PML layers not halved, or with the velocity
+    of the odd fine nodes all differ from the rediscretised level."""
+    c, p, h, omega = _coarse_case()
+    prob = iofd.make_problem(c, p, h, omega)
+    ref = iofd.make_problem(c[::2, ::2, ::2], p // 2, 2 * h, omega, nlevels=1).levels[0]
+    lev = prob.levels[1]
+    assert _same_level(lev, ref)
+    wrong_ell = dataclasses_replace(lev, kappa=omega * h / prob.c_ext[::2, ::2, ::2])
+    wrong_pml = dataclasses_replace(lev, pml=tuple(iofd.pml_1d(m, p, prob.gamma_max) for m in lev.n))
+    odd = np.ix_(*[np.minimum(2 * np.arange(m) + 1, 2 * (m - 1)) for m in lev.shape])
+    wrong_c = dataclasses_replace(lev, kappa=omega * 2 * h / prob.c_ext[odd])
+    assert wrong_c.kappa.shape == lev.kappa.shape
+    for bad in (wrong_ell, wrong_pml, wrong_c):
+        assert not _same_level(bad, ref)
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+    return dataclasses.replace(obj, **kw)
+
+
 def test_point_source_normalisation():
     w, prob = small_problem()
     F = iofd.point_sources(prob, [(3, 4, 5, 2.0 + 1.0j)])
