@@ -17,7 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhz.so")
-SOURCES = ["hz_stencil.cu", "hz_vec.cu", "hz_solver.cu"]
+# (source, extra flags, object): the forward stencil source is compiled once
+# per (precision, mode) part so that its kernels build in parallel
+SOURCES = [("hz_stencil.cu", [], "hz_stencil.o"), ("hz_vec.cu", [], "hz_vec.o"), ("hz_solver.cu", [], "hz_solver.o")] + [
+    ("hz_fwd.cu", [f"-DHZ_FWD_PART={k}"], f"hz_fwd_{k}.o") for k in range(5)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
@@ -44,12 +47,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
     headers.append(os.path.join(INCLUDE, "hz.h"))
     objs = []
     jobs = []
-    for src in SOURCES:
+    for src, extra, obj in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, obj)
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
+            jobs.append([nvcc] + ARCH + FLAGS + extra + ["-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -59,7 +62,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             raise RuntimeError(f"nvcc failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         for out in ex.map(run, jobs):
             if verbose and out:
                 print(out)

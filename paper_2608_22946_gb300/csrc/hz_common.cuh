@@ -129,6 +129,12 @@ struct LevelView {
   const R* kappa;                 // k(x_i) * ell per node
   const cx<R>* abar[3];
   const cx<R>* achk[3];
+  // PML correction factors of the forward kernel, per axis and node:
+  // eps[a][0] = -(abar - 1 + achk) / ell^2, eps[a][1] = -(abar - 1 - achk) / ell^2
+  // (zero where the axis is not stretched)
+  const cx<R>* eps[3][2];
+  // precombined coefficient polynomials of this level (layout in hz_fwd.cuh)
+  const R* ctab;
   int plain_lo[3], plain_hi[3];
   R inv_ell2;                     // 1 / ell^2
   int zblock;                     // planes per CTA of the forward stencil (0: heuristic)

@@ -1,0 +1,187 @@
+// Launch layout and launchers of the forward stencil (hz_fwd.cuh).
+#pragma once
+
+#include <algorithm>
+
+#include "hz_fwd.cuh"
+
+namespace hz {
+
+// Planes per block when neither the caller nor the tuner chose: about four
+// waves of two blocks on 152 SMs, at least kMinZblock planes.
+inline int choose_zblock(int nx, int ny, int nz, int nrhs) {
+  const long long tiles =
+      (long long)((nx + ShRect::TWN - 1) / ShRect::TWN) * ((ny + ShRect::TYT - 1) / ShRect::TYT) * nrhs;
+  const long long want = 152LL * 2 * 4;
+  const long long nzb = (want + tiles - 1) / tiles;
+  int zb = (int)((nz + nzb - 1) / nzb);
+  zb = std::max(zb, kMinZblock);
+  zb = std::min(zb, kMaxZb);
+  return zb;
+}
+
+// Grids of at least this many nodes split the A/B application into the
+// PML-free rectangle and the PML frame (two launches, each carrying only its
+// own row forms' registers); smaller grids, where launch latency dominates,
+// use one launch that chooses the row form per tile.
+constexpr long long kSplitNodes = 1LL << 20;
+
+inline int cdiv_i(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
+
+struct FwdPlan {
+  int zb = 4, nzb = 1;    // whole grid or rectangle
+  int zbf = 4, nzbf = 1;  // frame
+  bool split = false;
+  int GW = 1, GH = 1;     // whole-grid 64 x 8 tiles
+  int RW = 0, RH = 0;     // 64 x 8 tiles of the PML-free rectangle
+  TileMap frame;          // frame tiling (count = frame tiles per z-block)
+  long long blocks() const {
+    return split ? (long long)RW * RH * nzb + (long long)frame.count * nzbf : (long long)GW * GH * nzb;
+  }
+};
+
+inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* phi, bool ab, int zb, int zbf) {
+  FwdPlan p;
+  p.zb = std::min(std::min(zb, kMaxZb), nz);
+  p.nzb = (nz + p.zb - 1) / p.zb;
+  p.zbf = std::min(std::min(zbf > 0 ? zbf : zb, kMaxZb), nz);
+  p.nzbf = (nz + p.zbf - 1) / p.zbf;
+  p.GW = cdiv_i(nx, ShRect::TWN);
+  p.GH = cdiv_i(ny, ShRect::TYT);
+  const int px0 = std::max(plo[0], 0), px1 = std::min(phi[0], nx - 1);
+  const int py0 = std::max(plo[1], 0), py1 = std::min(phi[1], ny - 1);
+  p.split = ab && (long long)nx * ny * nz >= kSplitNodes && px1 >= px0 && py1 >= py0;
+  if (!p.split) return p;
+  p.RW = cdiv_i(px1 - px0 + 1, ShRect::TWN);
+  p.RH = cdiv_i(py1 - py0 + 1, ShRect::TYT);
+  TileMap& f = p.frame;
+  f.nx = nx;
+  f.ny = ny;
+  f.px0 = px0;
+  f.px1 = px1;
+  f.py0 = py0;
+  f.py1 = py1;
+  f.nwx = cdiv_i(nx, ShWide::TWN);
+  f.nw_lo = cdiv_i(py0, ShWide::TYT);
+  f.nw_hi = cdiv_i(ny - 1 - py1, ShWide::TYT);
+  f.nty = cdiv_i(py1 - py0 + 1, ShTall::TYT);
+  f.nt_lo = cdiv_i(px0, ShTall::TWN);
+  f.nt_hi = cdiv_i(nx - 1 - px1, ShTall::TWN);
+  f.count = f.nwx * (f.nw_lo + f.nw_hi) + f.nty * (f.nt_lo + f.nt_hi);
+  return p;
+}
+
+template <class R>
+inline FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, bool ab) {
+  const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, nrhs);
+  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f);
+}
+
+template <class R, int MODE, int OPK, int RB>
+void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
+  const LevelView<R>& L = c.lv;
+  const FwdPlan p = plan_fwd(L, c.nrhs, OPK != OPK_Q);
+  const int ng = c.nrhs / RB;
+  const int nblk_total = (int)p.blocks();
+  if (!p.split) {
+    TileMap tm;
+    tm.ntx = p.GW;
+    tm.nblk_total = nblk_total;
+    count_launch();
+    k_fwd_grid<R, MODE, OPK, RB><<<dim3(p.GW * ng, p.GH, p.nzb), ShRect::NT, fwd_smem_rect<R, MODE, OPK, RB>(), s>>>(
+        c, p.zb, tm);
+    return;
+  }
+  TileMap ti;
+  ti.ox = p.frame.px0;
+  ti.oy = p.frame.py0;
+  ti.ntx = p.RW;
+  ti.rx1 = p.frame.px1;
+  ti.ry1 = p.frame.py1;
+  ti.bid_offset = 0;
+  ti.nblk_total = nblk_total;
+  TileMap tp = p.frame;
+  tp.bid_offset = p.RW * p.RH * p.nzb;
+  tp.nblk_total = nblk_total;
+  // the two launches are independent (disjoint outputs; a fused norm combines
+  // through its arrival counter): with a side stream they run concurrently
+  const bool fork = c.side && c.fork && c.join && tp.count > 0;
+  cudaStream_t s2 = fork ? c.side : s;
+  if (fork) {
+    cudaEventRecord(c.fork, s);
+    cudaStreamWaitEvent(s2, c.fork, 0);
+  }
+  count_launch();
+  k_fwd_rect<R, MODE, OPK, RB><<<dim3(p.RW * ng, p.RH, p.nzb), ShRect::NT, fwd_smem_rect<R, MODE, OPK, RB>(), s>>>(
+      c, p.zb, ti);
+  if (tp.count > 0) {
+    count_launch();
+    k_fwd_frame<R, MODE, OPK, RB><<<dim3(tp.count * ng, 1, p.nzbf), ShWide::NT, fwd_smem_frame<R, MODE, OPK, RB>(),
+                                    s2>>>(c, p.zbf, tp);
+  }
+  if (fork) {
+    cudaEventRecord(c.join, s2);
+    cudaStreamWaitEvent(s, c.join, 0);
+  }
+}
+
+// right-hand sides per block: two for complex64 (the coefficients of three
+// rows and two accumulators per right-hand side stay in registers), one for
+// complex128 (its kernels are bound by the FP64 rate)
+template <class R, int MODE>
+constexpr int fwd_rb_max() {
+  return sizeof(R) == 8 ? 1 : 2;
+}
+inline int fwd_pick_rb(int nrhs, int rbmax) { return (rbmax >= 2 && nrhs % 2 == 0) ? 2 : 1; }
+
+template <class R, int MODE, int OPK>
+void launch_fwd_opk(const StencilCall<R>& c, cudaStream_t s) {
+  constexpr int RBM = fwd_rb_max<R, MODE>();
+  if constexpr (RBM >= 2) {
+    if (fwd_pick_rb(c.nrhs, RBM) == 2) {
+      launch_fwd_rb<R, MODE, OPK, 2>(c, s);
+      return;
+    }
+  }
+  launch_fwd_rb<R, MODE, OPK, 1>(c, s);
+}
+
+template <class R, int MODE, int OPK, int RB>
+void fwd_attrs_rb() {
+  cudaFuncSetAttribute(k_fwd_grid<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fwd_smem_rect<R, MODE, OPK, RB>());
+  if constexpr (OPK != OPK_Q) {
+    cudaFuncSetAttribute(k_fwd_rect<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem_rect<R, MODE, OPK, RB>());
+    cudaFuncSetAttribute(k_fwd_frame<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem_frame<R, MODE, OPK, RB>());
+  }
+}
+template <class R, int MODE, int OPK>
+void fwd_attrs_opk() {
+  fwd_attrs_rb<R, MODE, OPK, 1>();
+  if constexpr (fwd_rb_max<R, MODE>() >= 2) fwd_attrs_rb<R, MODE, OPK, 2>();
+}
+
+// Entry points of one (precision, mode): instantiated in hz_fwd.cu, one
+// translation unit per pair.
+template <class R, int MODE>
+void launch_fwd(const StencilCall<R>& c, int opk, cudaStream_t s) {
+  if constexpr (MODE == M_APPLY) {
+    if (opk == OPK_Q) {
+      launch_fwd_opk<R, MODE, OPK_Q>(c, s);
+      return;
+    }
+  }
+  if (opk == OPK_B) launch_fwd_opk<R, MODE, OPK_B>(c, s);
+  else launch_fwd_opk<R, MODE, OPK_A>(c, s);
+}
+
+template <class R, int MODE>
+void fwd_init_attrs() {
+  fwd_attrs_opk<R, MODE, OPK_A>();
+  fwd_attrs_opk<R, MODE, OPK_B>();
+  if constexpr (MODE == M_APPLY) fwd_attrs_opk<R, MODE, OPK_Q>();
+}
+
+}  // namespace hz

@@ -50,10 +50,18 @@ struct StencilCall {
 
 template <class R>
 void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cudaStream_t s);
-// Smallest z-block (planes per CTA) of a forward stencil launch.
+// Forward stencil of one (precision, mode) for operator kind opk (hz_fwd.cuh),
+// and the one-time kernel attributes of those kernels.
+template <class R, int MODE>
+void launch_fwd(const StencilCall<R>& c, int opk, cudaStream_t s);
+template <class R, int MODE>
+void fwd_init_attrs();
+// Smallest z-block (planes per CTA) of a stencil launch.
 constexpr int kMinZblock = 4;
 long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
                                  int zblock = 0, int zblock_f = 0);
+// Blocks per right-hand side of an adjoint stencil launch (zblock > 0 forces it).
+long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
 // Host replay of a forward stencil application's launch layout on a grid of
 // nx x ny x nz nodes: per-node write counts of right-hand side 0 (or null) and
 // the number of layout violations (defined beside the tiling).

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "hz.h"
+#include "hz_fwd.cuh"
 #include "hz_kernels.h"
 
 using namespace hz;
@@ -90,6 +91,12 @@ struct Level {
   cx<double>* achk_d[3] = {};
   cx<float>* abar_f[3] = {};
   cx<float>* achk_f[3] = {};
+  // PML correction factors eps+- of the forward kernel per axis, and the
+  // precombined coefficient polynomials of this level
+  cx<double>* eps_d[3][2] = {};
+  cx<float>* eps_f[3][2] = {};
+  double* ctab_d = nullptr;
+  float* ctab_f = nullptr;
   int plain_lo[3] = {}, plain_hi[3] = {};
   // 1/diag of the operator each Jacobi map of Algorithm 1 uses on this level
   // ([0]: A_L, [1]: B_L); complex64 set at creation, complex128 on first use
@@ -164,6 +171,8 @@ template <> struct Sel<float> {
   static const cx<float>* ac(const Level& L, int a) { return L.achk_f[a]; }
   static const float* tab(hz_handle* H) { return H->tab_f; }
   static const cx<float>* dinv(const Level& L, bool shifted) { return L.dinv_f[shifted ? 1 : 0]; }
+  static const cx<float>* eps(const Level& L, int a, int s) { return L.eps_f[a][s]; }
+  static const float* ctab(const Level& L) { return L.ctab_f; }
   static constexpr int prec = HZ_C64;
 };
 template <> struct Sel<double> {
@@ -173,6 +182,8 @@ template <> struct Sel<double> {
   static const cx<double>* ac(const Level& L, int a) { return L.achk_d[a]; }
   static const double* tab(hz_handle* H) { return H->tab_d; }
   static const cx<double>* dinv(const Level& L, bool shifted) { return L.dinv_d[shifted ? 1 : 0]; }
+  static const cx<double>* eps(const Level& L, int a, int s) { return L.eps_d[a][s]; }
+  static const double* ctab(const Level& L) { return L.ctab_d; }
   static constexpr int prec = HZ_C128;
 };
 
@@ -218,7 +229,7 @@ void build_table(const double* rows, int K, std::vector<double>& coef, double& d
     HZ_REQUIRE(std::fabs((rows[(k + 1) * 17] - rows[k * 17]) - ds) < 1e-9 * std::max(1.0, ds),
                "IOFD table nodes must be uniformly spaced");
   HZ_REQUIRE(std::fabs(rows[0]) < 1e-12, "IOFD table must start at s = 0");
-  HZ_REQUIRE(rows[(K - 1) * 17] >= kEtaMax - 1e-12, "IOFD table must reach s = 0.4");
+  HZ_REQUIRE(std::fabs(rows[(K - 1) * 17] - kEtaMax) < 1e-9, "IOFD table must end at s = 0.4");
   coef.assign((size_t)kMaxSeg * kNumFn * 4, 0.0);
   for (int k = 0; k + 1 < K; ++k) {
     for (int f = 0; f < kNumFn; ++f) {
@@ -236,6 +247,104 @@ void build_table(const double* rows, int K, std::vector<double>& coef, double& d
   }
 }
 
+// ----------------------------------------------------------------------------
+// precombined coefficient polynomials of the forward kernel (hz_fwd.cuh)
+// ----------------------------------------------------------------------------
+using Poly = std::array<double, 6>;  // power basis, degree <= 5
+
+Poly poly_shift(const double* c, int deg, double d) {  // p(u + d) of p(u) = sum c_i u^i
+  Poly out{};
+  for (int i = deg; i >= 0; --i) {  // Horner in polynomials: out = out * (u + d) + c_i
+    Poly t{};
+    for (int j = 0; j < 5; ++j) {
+      t[j + 1] += out[j];
+      t[j] += d * out[j];
+    }
+    t[0] += c[i];
+    out = t;
+  }
+  return out;
+}
+Poly poly_lin(double a0, const Poly& p, double s) {  // a0 + s p
+  Poly o{};
+  for (int j = 0; j < 6; ++j) o[j] = s * p[j];
+  o[0] += a0;
+  return o;
+}
+Poly poly_add(const Poly& a, const Poly& b, double sb) {  // a + sb b
+  Poly o{};
+  for (int j = 0; j < 6; ++j) o[j] = a[j] + sb * b[j];
+  return o;
+}
+Poly poly_mul_quad(const Poly& p, double q0, double q1, double q2) {  // p (q0 + q1 u + q2 u^2), deg p <= 3
+  Poly o{};
+  for (int j = 0; j < 4; ++j) {
+    o[j] += q0 * p[j];
+    o[j + 1] += q1 * p[j];
+    o[j + 2] += q2 * p[j];
+  }
+  return o;
+}
+
+// Coefficient polynomials of one level, laid out [kind][segment][power][function]
+// as hz_fwd.cuh describes.  On segment k the kernel evaluates at u = eta - s_o
+// with s_o = (R)k * (R)ds rounded as it rounds it (single: float, double:
+// double), so each Hermite cubic (power basis about the table node s_k) is
+// re-expanded about s_o and kappa^2 = (2 pi)^2 (s_o + u)^2.  Segment nseg
+// (eta >= 0.4) holds the clamped, constant alpha's and beta's.
+//   C_m = (L_m - kappa^2 M_m) / ell^2,  K_m = kappa^2 M_m / ell^2,
+//   L = (6 a4, a5 - a4, (1 - a4 - 2 a5) / 2, -3 (1 - a4 - a5) / 4),
+//   M = (a1, a2 / 6, a3 / 12, (1 - a1 - a2 - a3) / 8),
+//   Q = (b1, b2 / 6, b3 / 12, (1 - b1 - b2 - b3) / 8)
+// (Eq. iofd-shell-coefficients, Eq. q-operator).
+void build_coef_tables(const std::vector<double>& coef, const double* rows, int K, double ds, double ell,
+                       bool single, std::vector<double>& out) {
+  const int nseg = K - 1, ns = K;
+  out.assign((size_t)kCtPerSeg * ns, 0.0);
+  const double four_pi2 = 4.0 * M_PI * M_PI, inv_l2 = 1.0 / (ell * ell);
+  for (int k = 0; k <= nseg; ++k) {
+    const double s_o = single ? (double)((float)k * (float)ds) : (double)k * ds;
+    Poly P[kNumFn];
+    for (int f = 0; f < kNumFn; ++f) {
+      if (k < nseg) {
+        P[f] = poly_shift(&coef[((size_t)k * kNumFn + f) * 4], 3, s_o - rows[k * 17]);
+      } else {
+        P[f] = Poly{};
+        P[f][0] = rows[(K - 1) * 17 + (f < 5 ? 1 + f : 11 + (f - 5))];
+      }
+    }
+    const Poly &a1 = P[0], &a2 = P[1], &a3 = P[2], &a4 = P[3], &a5 = P[4], &b1 = P[5], &b2 = P[6], &b3 = P[7];
+    Poly Lm[4], Mm[4], Qm[4];
+    Lm[0] = poly_lin(0.0, a4, 6.0);
+    Lm[1] = poly_add(a5, a4, -1.0);
+    Lm[2] = poly_add(poly_lin(0.5, a4, -0.5), a5, -1.0);
+    Lm[3] = poly_add(poly_lin(-0.75, a4, 0.75), a5, 0.75);
+    Mm[0] = a1;
+    Mm[1] = poly_lin(0.0, a2, 1.0 / 6.0);
+    Mm[2] = poly_lin(0.0, a3, 1.0 / 12.0);
+    Mm[3] = poly_add(poly_add(poly_lin(0.125, a1, -0.125), a2, -0.125), a3, -0.125);
+    Qm[0] = b1;
+    Qm[1] = poly_lin(0.0, b2, 1.0 / 6.0);
+    Qm[2] = poly_lin(0.0, b3, 1.0 / 12.0);
+    Qm[3] = poly_add(poly_add(poly_lin(0.125, b1, -0.125), b2, -0.125), b3, -0.125);
+    // kappa^2 = (2 pi)^2 (s_o + u)^2
+    const double q0 = four_pi2 * s_o * s_o, q1 = 2.0 * four_pi2 * s_o, q2 = four_pi2;
+    for (int m = 0; m < 4; ++m) {
+      const Poly Km = poly_lin(0.0, poly_mul_quad(Mm[m], q0, q1, q2), inv_l2);
+      const Poly Cm = poly_add(poly_lin(0.0, Lm[m], inv_l2), Km, -1.0);
+      for (int j = 0; j < 6; ++j) {
+        out[(size_t)k * kCtCA + 4 * j + m] = Cm[j];
+        out[ct_off_K(ns) + (size_t)k * kCtK + 4 * j + m] = Km[j];
+      }
+      for (int j = 0; j < 4; ++j) out[ct_off_Q(ns) + (size_t)k * kCtQ + 4 * j + m] = Qm[m][j];
+    }
+    for (int j = 0; j < 4; ++j) {
+      out[ct_off_T(ns) + (size_t)k * kCtT + 2 * j] = a4[j];
+      out[ct_off_T(ns) + (size_t)k * kCtT + 2 * j + 1] = a5[j];
+    }
+  }
+}
+
 template <class R>
 LevelView<R> view(hz_handle* H, int L) {
   const Level& lv = H->lev[L];
@@ -248,9 +357,12 @@ LevelView<R> view(hz_handle* H, int L) {
   for (int a = 0; a < 3; ++a) {
     v.abar[a] = Sel<R>::ab(lv, a);
     v.achk[a] = Sel<R>::ac(lv, a);
+    v.eps[a][0] = Sel<R>::eps(lv, a, 0);
+    v.eps[a][1] = Sel<R>::eps(lv, a, 1);
     v.plain_lo[a] = lv.plain_lo[a];
     v.plain_hi[a] = lv.plain_hi[a];
   }
+  v.ctab = Sel<R>::ctab(lv);
   v.inv_ell2 = (R)(1.0 / (lv.ell * lv.ell));
   v.zblock = lv.zblock;
   v.zblock_f = lv.zblock_f;
@@ -643,15 +755,23 @@ void level_dims(const hz_grid& g, int L, Level& lv) {
   for (int a = 0; a < 3; ++a) pml_axis(nn[a], lv.n_pml, g.gamma_max, ab, ac, lv.plain_lo[a], lv.plain_hi[a]);
 }
 
+// Block partial sums of one fused stencil reduction (forward or adjoint
+// launch) on level lv with nrhs right-hand sides, at the z-blocks it will run.
+long long resid_blocks(const Level& lv, int nrhs, bool adjoint) {
+  return adjoint ? adj_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs)
+                 : stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nrhs, lv.zblock, lv.zblock_f);
+}
+
 // Per-block partial sums: the vector reductions use at most 1216 x 56, a fused
-// stencil reduction one per block at the smallest z-block (4 planes) the
-// launch planner or the autotuner can pick.
+// stencil reduction one per block -- forward or adjoint launch -- at the
+// smallest z-block (4 planes) the planners or the autotuner can pick.
 size_t red_partial_size(const Level* lev, int nrhs) {
   size_t m = 1216 * 56;
   for (int L = 0; L < 3; ++L) {
-    const long long t = stencil_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, lev[L].plain_lo, lev[L].plain_hi, 1,
+    const long long f = stencil_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, lev[L].plain_lo, lev[L].plain_hi, 1,
                                                kMinZblock, kMinZblock);
-    m = std::max(m, (size_t)t);
+    const long long a = adj_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, 1, kMinZblock);
+    m = std::max(m, (size_t)std::max(f, a));
   }
   return m * nrhs;
 }
@@ -671,7 +791,13 @@ void plan_all(hz_handle* H, bool count_only) {
       lv.achk_d[a] = al.get<cx<double>>(nn[a]);
       lv.abar_f[a] = al.get<cx<float>>(nn[a]);
       lv.achk_f[a] = al.get<cx<float>>(nn[a]);
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        lv.eps_d[a][sgn] = al.get<cx<double>>(nn[a]);
+        lv.eps_f[a][sgn] = al.get<cx<float>>(nn[a]);
+      }
     }
+    lv.ctab_d = al.get<double>((size_t)kCtPerSeg * (kMaxSeg + 1));
+    lv.ctab_f = al.get<float>((size_t)kCtPerSeg * (kMaxSeg + 1));
   }
   H->lev[0].dinv_f[0] = al.get<cx<float>>(H->lev[0].N);
   H->lev[1].dinv_f[1] = al.get<cx<float>>(H->lev[1].N);
@@ -1170,6 +1296,25 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
         HZ_CK(cudaMemcpy(lv.achk_d[a], ac.data(), ac.size() * 16, cudaMemcpyHostToDevice));
         HZ_CK(cudaMemcpy(lv.abar_f[a], abf.data(), abf.size() * 8, cudaMemcpyHostToDevice));
         HZ_CK(cudaMemcpy(lv.achk_f[a], acf.data(), acf.size() * 8, cudaMemcpyHostToDevice));
+        // eps+- = -(abar - 1 +- achk) / ell^2: zero where the axis is not stretched
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          std::vector<std::complex<double>> e(ab.size());
+          std::vector<cx<float>> ef(ab.size());
+          for (size_t i = 0; i < ab.size(); ++i) {
+            e[i] = -((ab[i] - 1.0) + (sgn == 0 ? ac[i] : -ac[i])) / (lv.ell * lv.ell);
+            ef[i] = mkc<float>((float)e[i].real(), (float)e[i].imag());
+          }
+          HZ_CK(cudaMemcpy(lv.eps_d[a][sgn], e.data(), e.size() * 16, cudaMemcpyHostToDevice));
+          HZ_CK(cudaMemcpy(lv.eps_f[a][sgn], ef.data(), ef.size() * 8, cudaMemcpyHostToDevice));
+        }
+      }
+      {
+        std::vector<double> ct_d, ct_s;
+        build_coef_tables(coef, table_host, table_rows, ds, lv.ell, false, ct_d);
+        build_coef_tables(coef, table_host, table_rows, ds, lv.ell, true, ct_s);
+        std::vector<float> ct_f(ct_s.begin(), ct_s.end());
+        HZ_CK(cudaMemcpy(lv.ctab_d, ct_d.data(), ct_d.size() * sizeof(double), cudaMemcpyHostToDevice));
+        HZ_CK(cudaMemcpy(lv.ctab_f, ct_f.data(), ct_f.size() * sizeof(float), cudaMemcpyHostToDevice));
       }
       launch_setup_kappa<double>(c_dev, H->g.nx + 1, H->g.ny + 1, H->g.nz + 1, H->g.n_pml, f, H->g.omega, lv.ell,
                                  lv.kap_d, H->st);
@@ -1482,10 +1627,13 @@ namespace {
 
 constexpr long long kResidStaticPartials = 1 << 16;  // doubles (512 KiB)
 constexpr int kResidStaticMaxRhs = 64;
-// [partials (kResidStaticPartials) | norm2 staging (64) | counters (64, as unsigned)]
-static __device__ __align__(256) double g_resid_static[kResidStaticPartials + 2 * kResidStaticMaxRhs];
+// [partials (kResidStaticPartials) | arrival counters (64 unsigned, in 32 double slots)]
+static __device__ __align__(256) double g_resid_static[kResidStaticPartials + kResidStaticMaxRhs / 2];
 
 constexpr int kMaxDevices = 64;
+// Device address of the array per device, written by the first call on that
+// device; threads racing on that first call all write the same address, so no
+// lock is taken.
 double* g_resid_static_addr[kMaxDevices] = {};
 
 // Host-side stand-in -> device address, once per device (with that device current).
@@ -1515,8 +1663,9 @@ extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int p
     HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
     HZ_REQUIRE(nrhs <= kResidStaticMaxRhs, "nrhs exceeds the static scratch limit of 64 right-hand sides");
     const Level& lv = H->lev[level];
-    const long long need =
-        stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nrhs, lv.zblock, lv.zblock_f) * nrhs;
+    const bool adj0 = (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ);
+    // partial sums of the launch that will run (forward and adjoint tile differently)
+    const long long need = resid_blocks(lv, nrhs, adj0) * nrhs;
     HZ_REQUIRE(need <= kResidStaticPartials,
                "grid too large for the static scratch (" + std::to_string(need) + " block partial sums > " +
                    std::to_string(kResidStaticPartials) + ")");
@@ -1525,10 +1674,10 @@ extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int p
     Reduce red;
     red.partial = base;
     red.out = norm2;
-    red.count = reinterpret_cast<unsigned*>(base + kResidStaticPartials + kResidStaticMaxRhs);
+    red.count = reinterpret_cast<unsigned*>(base + kResidStaticPartials);
     // the arrival counters must start at zero (the last block also resets them)
     HZ_CK(cudaMemsetAsync(red.count, 0, sizeof(unsigned) * nrhs, st));
-    const bool adj = (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ);
+    const bool adj = adj0;
     const bool shifted = (op == HZ_OP_B || op == HZ_OP_B_ADJ);
     if (precision == HZ_C64) {
       StencilCall<float> c = call<float>(H, level, shifted, nrhs);
