@@ -683,9 +683,10 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
 // ----------------------------------------------------------------------------
 // kernels
 // ----------------------------------------------------------------------------
+// resident blocks per SM the register allocation targets (128 registers a thread)
 template <class R, int RB, int NT>
 struct FMinB {
-  static constexpr int v = sizeof(R) == 8 ? 1 : (NT == 256 ? (RB == 1 ? 3 : 2) : (RB == 1 ? 4 : 4));
+  static constexpr int v = sizeof(R) == 8 ? 1 : (NT == 256 ? 2 : 4);
 };
 
 // the PML-free rectangle (shell rows)
