@@ -109,10 +109,11 @@ struct FLayout {
 // Which tiles a launch covers.  Rectangle / grid launches: tile (t, blockIdx.y)
 // has its origin at (ox + 64 t, oy + 8 blockIdx.y) and writes columns up to
 // (rx1, ry1).  Frame launches: the PML frame around the PML-free rectangle
-// [px0, px1] x [py0, py1], as rows of 64 x 4 tiles below and above it (full x
-// range) followed by rows of 4 x 32 tiles left and right of it (its y range).
-// All launches of one operator application share one block numbering
-// (bid_offset, nblk_total) so that a fused grid reduction spans them.
+// [px0, px1] x [py0, py1], as rows of 64 x 4 tiles below and above it (its x
+// range; only y is stretched there) followed by columns of 4 x 32 tiles left
+// and right of it (all y; x and, in the corners, y stretched).  All launches
+// of one operator application share one block numbering (bid_offset,
+// nblk_total) so that a fused grid reduction spans them.
 struct TileMap {
   int ox = 0, oy = 0, ntx = 1, rx1 = 0, ry1 = 0;
   int nx = 0, ny = 0, px0 = 0, px1 = -1, py0 = 0, py1 = -1;
@@ -132,8 +133,8 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
   const int nw = m.nwx * (m.nw_lo + m.nw_hi);
   if (t < nw) {
     const int r = t / m.nwx, c = t - r * m.nwx;
-    f.x0 = c * ShWide::TWN;
-    f.rx1 = m.nx - 1;
+    f.x0 = m.px0 + c * ShWide::TWN;
+    f.rx1 = m.px1;
     if (r < m.nw_lo) {
       f.y0 = r * ShWide::TYT;
       f.ry1 = m.py0 - 1;
@@ -145,8 +146,8 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
   } else {
     const int u = t - nw, per = m.nt_lo + m.nt_hi;
     const int r = u / per, c = u - r * per;
-    f.y0 = m.py0 + r * ShTall::TYT;
-    f.ry1 = m.py1;
+    f.y0 = r * ShTall::TYT;
+    f.ry1 = m.ny - 1;
     if (c < m.nt_lo) {
       f.x0 = c * ShTall::TWN;
       f.rx1 = m.px0 - 1;
@@ -159,12 +160,12 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
   return f;
 }
 
-// Row form of a whole-grid tile: 0 shell, 1 x stretched, 3 y stretched, 2 both.
+// Row form of a whole-grid tile: 0 shell (x and y outside the PML), 2 general.
 __host__ __device__ __forceinline__ int grid_tile_form(int x0, int y0, int nx, int ny, const int* plo,
                                                       const int* phi) {
   const int xe = min(x0 + ShRect::TWN - 1, nx - 1), ye = min(y0 + ShRect::TYT - 1, ny - 1);
   const bool px = x0 >= plo[0] && xe <= phi[0], py = y0 >= plo[1] && ye <= phi[1];
-  return (px && py) ? 0 : (py ? 1 : (px ? 3 : 2));
+  return (px && py) ? 0 : 2;
 }
 
 // ----------------------------------------------------------------------------
@@ -300,7 +301,7 @@ __device__ __forceinline__ int t_block(int ns) { return OPK == OPK_B ? ct_off_T(
 // Contribution of one plane to a row at plane offset RHO (= plane - row):
 // shell weights, PML corrections in x / y (Ac, Bc) and, in a z-PML row, the z
 // correction eps * T_z with the row's own transverse weights.
-template <int RHO, bool CORR, class R, class CT>
+template <int RHO, bool CORR, bool ZP, class R, class CT>
 __device__ __forceinline__ cx<R> contrib(const CT& C, const RowT<R>& T, cx<R> c, cx<R> e, cx<R> k, cx<R> Ac,
                                          cx<R> Bc, bool zp, cx<R> ez) {
   cx<R> h;
@@ -322,11 +323,13 @@ __device__ __forceinline__ cx<R> contrib(const CT& C, const RowT<R>& T, cx<R> c,
       cfma(h, T.qb, Bc);
     }
   }
-  if (zp) {
-    cx<R> tau = cmulw(T.a4, c);
-    cfma(tau, T.q5, e);
-    cfma(tau, T.qb, k);
-    h += ez * tau;
+  if constexpr (ZP) {
+    if (zp) {
+      cx<R> tau = cmulw(T.a4, c);
+      cfma(tau, T.q5, e);
+      cfma(tau, T.qb, k);
+      h += ez * tau;
+    }
   }
   return h;
 }
@@ -335,18 +338,19 @@ __device__ __forceinline__ cx<R> contrib(const CT& C, const RowT<R>& T, cx<R> c,
 // one block: tile (x0, y0) of shape TS writing columns up to (rx1, ry1), z-block
 // blockIdx.z, right-hand sides rhs0 .. rhs0 + RB - 1
 // ----------------------------------------------------------------------------
-// FORM: 0 shell (x and y outside the PML), 1 x stretched, 3 y stretched, 2 both.
-// z-PML rows are handled inside every form.
-template <class R, int MODE, int OPK, int FORM, class TS, int RB>
+// FORM: 0 shell (x and y outside the PML), 3 y stretched, 2 x and y stretched.
+// ZP: some row of the block lies in the z-PML (blocks wholly between the two
+// z-layers carry no z-correction code at all).
+template <class R, int MODE, int OPK, int FORM, bool ZP, class TS, int RB>
 __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char* smem, int zblock, int x0, int y0,
                                          int rx1, int ry1, int rhs0, unsigned bid, unsigned nblk) {
   using LY = FLayout<R, MODE, OPK, TS, RB>;
   constexpr int NSTG = LY::NSTG, PREF = NSTG - 2;
   constexpr int NPX = TS::NPX, PWS = TS::PWS, PLN = TS::PLN, NT = TS::NT, NSLOT = TS::NSLOT;
   constexpr bool CPLX = OPK == OPK_B;
-  constexpr bool XC = FORM == 1 || FORM == 2, YC = FORM == 2 || FORM == 3, CORR = XC || YC;
-  constexpr bool ZC = OPK != OPK_Q;
-  static_assert(6 % NSTG == 0 && PREF >= 1, "ring depth must divide the unroll of 6");
+  constexpr bool XC = FORM == 2, YC = FORM == 2 || FORM == 3, CORR = XC || YC;
+  static_assert(PREF >= 1, "ring too short");
+  static_assert(!ZP || OPK != OPK_Q, "Q_h has no PML terms");
   using CT = RowC<R, CPLX>;
 
   const LevelView<R>& Lv = a.lv;
@@ -377,13 +381,15 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
     } else {
       const int nca = (kCtCA + (CPLX ? kCtK : 0)) * ns;
       for (int i = tid; i < nca; i += NT) sT[i] = g[i];
-      for (int i = tid; i < kCtT * ns; i += NT) sT[nca + i] = g[ct_off_T(ns) + i];
-      for (int t = tid; t < nplanes; t += NT) {
-        const int r = zb0 - 1 + t;
-        const bool ok = r >= 0 && r < nz;
-        sEz[2 * t] = ok ? Lv.eps[2][0][r] : mkc<R>(0, 0);
-        sEz[2 * t + 1] = ok ? Lv.eps[2][1][r] : mkc<R>(0, 0);
-      }
+      if constexpr (CORR || ZP)
+        for (int i = tid; i < kCtT * ns; i += NT) sT[nca + i] = g[ct_off_T(ns) + i];
+      if constexpr (ZP)
+        for (int t = tid; t < nplanes; t += NT) {
+          const int r = zb0 - 1 + t;
+          const bool ok = r >= 0 && r < nz;
+          sEz[2 * t] = ok ? Lv.eps[2][0][r] : mkc<R>(0, 0);
+          sEz[2 * t + 1] = ok ? Lv.eps[2][1][r] : mkc<R>(0, 0);
+        }
     }
   }
 
@@ -423,8 +429,8 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   }
   auto slot_ok = [&](int j) { return j < NSLOT - 1 || tid + j * NT < PLN; };
 
-  // group kk: halo plane zb0-1+kk of every right-hand side (and of 1/diag for
-  // the Jacobi map), kappa of the tile's own columns one plane higher
+  // group kk (ring stage st): halo plane zb0-1+kk of every right-hand side (and
+  // of 1/diag for the Jacobi map), kappa of the tile's own columns one plane higher
   auto issue = [&](int kk, int st) {
     const int q = zb0 - 1 + kk;
     const bool zin = (unsigned)q < (unsigned)nz;
@@ -461,49 +467,45 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
     else fcp_commit();
   }
 
-  // accumulators of rows p and p+1 (slot = row parity), coefficients of rows
-  // p-1, p, p+1 (slot = row mod 3); PML tiles also hold the rows' transverse
-  // weights, shell tiles only their kappa (the weights are needed on z-PML
-  // planes alone and are evaluated there)
+  // accumulators of rows p (role 0 this step) and p-1 / p+1 (completed, then
+  // reopened); coefficients of rows p-1, p, p+1 (slot = row mod 3).  PML tiles
+  // also hold the rows' transverse weights; shell tiles in a z-PML block hold
+  // the rows' kappa and evaluate the weights where a z-correction needs them.
   constexpr bool HOLD_T = CORR;
-  cx<R> acc[RB][2][NPX];
+  constexpr bool HOLD_K = !CORR && ZP;
+  cx<R> accP[RB][NPX], accM[RB][NPX];
   CT C[3][NPX];
   RowT<R> Th[HOLD_T ? 3 : 1][NPX];
-  R kq[(!HOLD_T && ZC) ? 3 : 1][NPX];
+  R kq[HOLD_K ? 3 : 1][NPX];
   R nrm2[RB];
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
     nrm2[r] = 0;
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < NPX; ++i) acc[r][s][i] = mkc<R>(0, 0);
+    for (int i = 0; i < NPX; ++i) accP[r][i] = accM[r][i] = mkc<R>(0, 0);
   }
 #pragma unroll
-  for (int s = 0; s < (HOLD_T ? 3 : 1); ++s)
+  for (int sl = 0; sl < (HOLD_T ? 3 : 1); ++sl)
 #pragma unroll
-    for (int i = 0; i < NPX; ++i) Th[s][i] = RowT<R>{0, 0, 0};
+    for (int i = 0; i < NPX; ++i) Th[sl][i] = RowT<R>{0, 0, 0};
   const R* tT = sT + t_block<OPK>(ns);
   const R om = a.omega_j;
   const int lc0 = (ty + 1) * PWS + NPX * tx + 1;  // halo index of this thread's first column
+  int st = 0, stp = NSTG - 1, sti = PREF;       // ring stages of planes k, k-1 and k+PREF
 
   auto step = [&](auto Uc, int k) {
-    constexpr int U = decltype(Uc)::value;                   // k mod 6
-    constexpr int S = U % NSTG, SP = (U + NSTG - 1) % NSTG;  // stages of planes k and k-1
-    constexpr int A0 = U & 1, A1 = A0 ^ 1;                    // accumulator slots of rows p and p +- 1
-    constexpr int CP = U % 3, CN = (U + 1) % 3, CM = (U + 2) % 3;  // coefficient slots of rows p, p+1, p-1
+    constexpr int U = decltype(Uc)::value;                          // k mod 3
+    constexpr int CP = U, CN = (U + 1) % 3, CM = (U + 2) % 3;      // coefficient slots of rows p, p+1, p-1
     fcp_wait<PREF - 1>();
     __syncthreads();
-    if (k + PREF < nplanes) issue(k + PREF, (S + PREF) % NSTG);
+    if (k + PREF < nplanes) issue(k + PREF, sti);
     else fcp_commit();
     const int p = zb0 - 1 + k;             // plane that arrived
     const bool o1 = k + 3 <= nplanes;      // row p+1 lies in this z-block
     const bool o0 = k >= 1 && k + 2 <= nplanes;
     const bool o3 = k >= 2;                // row p-1 completes
-    // rows of this block inside the z-PML (uniform)
-    const bool zq1 = ZC && o1 && (p + 1 < zlo || p + 1 > zhi);
-    const bool zq0 = ZC && o0 && (p < zlo || p > zhi);
-    const bool zq3 = ZC && o3 && (p - 1 < zlo || p - 1 > zhi);
+    const cx<R>* Xs = sX + (size_t)st * RB * PLN;
+    const cx<R>* Xsp = sX + (size_t)stp * RB * PLN;
 
     // own-column values of row p-1 read early (their latency overlaps the step)
     cx<R> gq[RB][NPX];
@@ -522,7 +524,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
     // coefficients of row p+1 (kappa arrived with this plane's group)
     if (o1) {
       R kv[NPX];
-      const R* kp = sK + ((size_t)S * NT + tid) * NPX;
+      const R* kp = sK + ((size_t)st * NT + tid) * NPX;
 #pragma unroll
       for (int i = 0; i < NPX; ++i) kv[i] = kp[i];
 #pragma unroll
@@ -531,10 +533,13 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
         const int seg = seg_of(kv[i], ns, ds, inv_ds, u);
         eval_c<R, OPK>(sT, ns, seg, u, a.mass_shift, C[CN][i]);
         if constexpr (HOLD_T) Th[CN][i] = eval_t(tT, seg, u);
-        else if constexpr (ZC) kq[CN][i] = kv[i];
+        if constexpr (HOLD_K) kq[CN][i] = kv[i];
       }
     }
-    // transverse weights of rows p-1, p, p+1 in this step
+
+    // z-PML rows among p-1, p, p+1 (uniform) and their correction factors
+    bool zq3 = false, zq0 = false, zq1 = false;
+    cx<R> ez3 = mkc<R>(0, 0), ez0 = mkc<R>(0, 0), ez1 = mkc<R>(0, 0);
     RowT<R> T3[NPX], T0[NPX], T1[NPX];
 #pragma unroll
     for (int i = 0; i < NPX; ++i) {
@@ -542,41 +547,46 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
         T3[i] = Th[CM][i];
         T0[i] = Th[CP][i];
         T1[i] = Th[CN][i];
-      } else if constexpr (ZC) {
-        const RowT<R> z{0, 0, 0};
-        R u;
-        T3[i] = zq3 ? eval_t(tT, seg_of(kq[CM][i], ns, ds, inv_ds, u), u) : z;
-        T0[i] = zq0 ? eval_t(tT, seg_of(kq[CP][i], ns, ds, inv_ds, u), u) : z;
-        T1[i] = zq1 ? eval_t(tT, seg_of(kq[CN][i], ns, ds, inv_ds, u), u) : z;
       } else {
         T3[i] = T0[i] = T1[i] = RowT<R>{0, 0, 0};
+      }
+    }
+    if constexpr (ZP) {
+      zq1 = o1 && (p + 1 < zlo || p + 1 > zhi);
+      zq0 = o0 && (p < zlo || p > zhi);
+      zq3 = o3 && (p - 1 < zlo || p - 1 > zhi);
+      // sEz[2 t + {0, 1}] = eps+, eps- of row zb0 - 1 + t; row p is t = k
+      if (zq3) ez3 = sEz[2 * (k - 1)];
+      if (zq0) ez0 = -(sEz[2 * k] + sEz[2 * k + 1]);
+      if (zq1) ez1 = sEz[2 * (k + 1) + 1];
+      if constexpr (HOLD_K) {
+#pragma unroll
+        for (int i = 0; i < NPX; ++i) {
+          R u;
+          if (zq3) T3[i] = eval_t(tT, seg_of(kq[CM][i], ns, ds, inv_ds, u), u);
+          if (zq0) T0[i] = eval_t(tT, seg_of(kq[CP][i], ns, ds, inv_ds, u), u);
+          if (zq1) T1[i] = eval_t(tT, seg_of(kq[CN][i], ns, ds, inv_ds, u), u);
+        }
       }
     }
 
     // Jacobi map: first sweep y1 = omega D^-1 g on the whole halo plane
     if constexpr (MODE == M_J2) {
+      const cx<R>* Ds = sD + (size_t)st * PLN;
 #pragma unroll
       for (int j = 0; j < NSLOT; ++j) {
         if (!slot_ok(j)) continue;
         const int li = tid + j * NT;
-        const cx<R> d = sD[(size_t)S * PLN + li];
+        const cx<R> d = Ds[li];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) sY1[(size_t)r * PLN + li] = om * (d * sX[((size_t)S * RB + r) * PLN + li]);
+        for (int r = 0; r < RB; ++r) sY1[(size_t)r * PLN + li] = om * (d * Xs[(size_t)r * PLN + li]);
       }
       __syncthreads();
     }
 
-    cx<R> ez3 = mkc<R>(0, 0), ez0 = mkc<R>(0, 0), ez1 = mkc<R>(0, 0);
-    if constexpr (ZC) {
-      // sEz[2 t + {0, 1}] = eps+, eps- of row zb0 - 1 + t; row p is t = k
-      if (zq3) ez3 = sEz[2 * (k - 1)];
-      if (zq0) ez0 = -(sEz[2 * k] + sEz[2 * k + 1]);
-      if (zq1) ez1 = sEz[2 * (k + 1) + 1];
-    }
-
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const cx<R>* P = (MODE == M_J2) ? sY1 + (size_t)r * PLN : sX + ((size_t)S * RB + r) * PLN;
+      const cx<R>* P = (MODE == M_J2) ? sY1 + (size_t)r * PLN : Xs + (size_t)r * PLN;
       cx<R> v[3][NPX + 2];
 #pragma unroll
       for (int row = 0; row < 3; ++row) {
@@ -618,7 +628,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
           cfma(Bc, exm_[i], Vm);
         }
         if (o3) {
-          const cx<R> h = acc[r][A1][i] + contrib<+1, CORR>(C[CM][i], T3[i], c, e, kk, Ac, Bc, zq3, ez3);
+          const cx<R> h = accM[r][i] + contrib<+1, CORR, ZP>(C[CM][i], T3[i], c, e, kk, Ac, Bc, zq3, ez3);
           if (act[i]) {
             const int idx = (p - 1) * plane_sz + col0 + i;
             cx<R> out;
@@ -628,32 +638,41 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
               out = gq[r][i] - h;
               nrm2[r] += abs2(out);
             } else if constexpr (MODE == M_J2) {
-              const cx<R> g0 = sX[((size_t)SP * RB + r) * PLN + lc0 + i];
-              const cx<R> d0 = sD[(size_t)SP * PLN + lc0 + i];
+              const cx<R> g0 = Xsp[(size_t)r * PLN + lc0 + i];
+              const cx<R> d0 = sD[(size_t)stp * PLN + lc0 + i];
               out = om * (d0 * g0) + om * (d0 * (g0 - h));
               if (a.base) out += gq[r][i];
             } else {  // M_JSWEEP
-              const cx<R> x0c = sX[((size_t)SP * RB + r) * PLN + lc0 + i];
+              const cx<R> x0c = Xsp[(size_t)r * PLN + lc0 + i];
               const cx<R> d0 = a.dinv[idx];
               out = x0c + om * (d0 * (gq[r][i] - h));
             }
             a.y[(size_t)(rhs0 + r) * (size_t)N + idx] = out;
           }
         }
-        if (o0) acc[r][A0][i] += contrib<0, CORR>(C[CP][i], T0[i], c, e, kk, Ac, Bc, zq0, ez0);
-        if (o1) acc[r][A1][i] = contrib<-1, CORR>(C[CN][i], T1[i], c, e, kk, Ac, Bc, zq1, ez1);
+        if (o0) accP[r][i] += contrib<0, CORR, ZP>(C[CP][i], T0[i], c, e, kk, Ac, Bc, zq0, ez0);
+        if (o1) accM[r][i] = contrib<-1, CORR, ZP>(C[CN][i], T1[i], c, e, kk, Ac, Bc, zq1, ez1);
       }
     }
+    // row p+1 (now in accM) is next step's role-0 row; row p becomes its row to complete
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int i = 0; i < NPX; ++i) {
+        const cx<R> t = accP[r][i];
+        accP[r][i] = accM[r][i];
+        accM[r][i] = t;
+      }
+    stp = st;
+    st = (st + 1 == NSTG) ? 0 : st + 1;
+    sti = (sti + 1 == NSTG) ? 0 : sti + 1;
   };
 
-  for (int k0 = 0; k0 < nplanes; k0 += 6) {
+  for (int k0 = 0; k0 < nplanes; k0 += 3) {
     // each step is skipped past the last plane (uniform across the block)
     if (k0 + 0 < nplanes) step(std::integral_constant<int, 0>{}, k0 + 0);
     if (k0 + 1 < nplanes) step(std::integral_constant<int, 1>{}, k0 + 1);
     if (k0 + 2 < nplanes) step(std::integral_constant<int, 2>{}, k0 + 2);
-    if (k0 + 3 < nplanes) step(std::integral_constant<int, 3>{}, k0 + 3);
-    if (k0 + 4 < nplanes) step(std::integral_constant<int, 4>{}, k0 + 4);
-    if (k0 + 5 < nplanes) step(std::integral_constant<int, 5>{}, k0 + 5);
   }
   fcp_wait<0>();
 
@@ -680,10 +699,17 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   }
 }
 
+// does any output row of z-block bz lie in the z-PML?
+template <class R>
+__device__ __forceinline__ bool block_in_zpml(const LevelView<R>& L, int zblock) {
+  const int zb0 = blockIdx.z * zblock, zb1 = min(zb0 + zblock, L.nz);
+  return zb0 < L.plain_lo[2] || zb1 - 1 > L.plain_hi[2];
+}
+
 // ----------------------------------------------------------------------------
 // kernels
 // ----------------------------------------------------------------------------
-// resident blocks per SM the register allocation targets (128 registers a thread)
+// resident blocks per SM the register allocation targets
 template <class R, int RB, int NT>
 struct FMinB {
   static constexpr int v = sizeof(R) == 8 ? 1 : (NT == 256 ? 2 : 4);
@@ -697,11 +723,16 @@ __global__ void __launch_bounds__(ShRect::NT, FMinB<R, RB, ShRect::NT>::v) k_fwd
   const int ng = a.nrhs / RB;
   const int g = blockIdx.x % ng, t = blockIdx.x / ng;
   const unsigned bid = (unsigned)(tm.bid_offset + t + tm.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
-  fwd_tile<R, MODE, OPK, 0, ShRect, RB>(a, fsm, zblock, tm.ox + t * ShRect::TWN, tm.oy + (int)blockIdx.y * ShRect::TYT,
-                                        tm.rx1, tm.ry1, g * RB, bid, (unsigned)tm.nblk_total);
+  const int x0 = tm.ox + t * ShRect::TWN, y0 = tm.oy + (int)blockIdx.y * ShRect::TYT;
+  const unsigned nb = (unsigned)tm.nblk_total;
+  if (block_in_zpml(a.lv, zblock))
+    fwd_tile<R, MODE, OPK, 0, true, ShRect, RB>(a, fsm, zblock, x0, y0, tm.rx1, tm.ry1, g * RB, bid, nb);
+  else
+    fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, tm.rx1, tm.ry1, g * RB, bid, nb);
 }
 
-// the PML frame around it
+// the PML frame around it: strips below and above the rectangle (y stretched)
+// and left and right of it (x stretched, y too in the corners)
 template <class R, int MODE, int OPK, int RB>
 __global__ void __launch_bounds__(ShWide::NT, FMinB<R, RB, ShWide::NT>::v) k_fwd_frame(StencilCall<R> a, int zblock,
                                                                                          TileMap tm) {
@@ -711,19 +742,14 @@ __global__ void __launch_bounds__(ShWide::NT, FMinB<R, RB, ShWide::NT>::v) k_fwd
   const int g = blockIdx.x % ng, t = blockIdx.x / ng;
   const FrameTile f = decode_frame(tm, t);
   const unsigned bid = (unsigned)(tm.bid_offset + t + tm.count * blockIdx.z);
+  const unsigned nb = (unsigned)tm.nblk_total;
+  const bool zp = block_in_zpml(a.lv, zblock);
   if (f.wide) {
-    // strips below / above the rectangle: only y is stretched away from the corners
-    const bool xplain = f.x0 >= a.lv.plain_lo[0] && f.x0 + ShWide::TWN - 1 <= a.lv.plain_hi[0];
-    if (xplain)
-      fwd_tile<R, MODE, OPK, 3, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid,
-                                            (unsigned)tm.nblk_total);
-    else
-      fwd_tile<R, MODE, OPK, 2, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid,
-                                            (unsigned)tm.nblk_total);
+    if (zp) fwd_tile<R, MODE, OPK, 3, true, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 3, false, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
   } else {
-    // strips left / right of it lie in its y range: only x is stretched
-    fwd_tile<R, MODE, OPK, 1, ShTall, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid,
-                                          (unsigned)tm.nblk_total);
+    if (zp) fwd_tile<R, MODE, OPK, 2, true, ShTall, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 2, false, ShTall, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
   }
 }
 
@@ -740,13 +766,14 @@ __global__ void __launch_bounds__(ShRect::NT, sizeof(R) == 8 ? 1 : 2) k_fwd_grid
   const int rx1 = a.lv.nx - 1, ry1 = a.lv.ny - 1;
   const unsigned nb = (unsigned)tm.nblk_total;
   if constexpr (OPK == OPK_Q) {
-    fwd_tile<R, MODE, OPK, 0, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
+    fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
   } else {
-    switch (grid_tile_form(x0, y0, a.lv.nx, a.lv.ny, a.lv.plain_lo, a.lv.plain_hi)) {
-      case 0: fwd_tile<R, MODE, OPK, 0, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb); break;
-      case 1: fwd_tile<R, MODE, OPK, 1, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb); break;
-      case 3: fwd_tile<R, MODE, OPK, 3, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb); break;
-      default: fwd_tile<R, MODE, OPK, 2, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb); break;
+    const bool zp = block_in_zpml(a.lv, zblock);
+    if (grid_tile_form(x0, y0, a.lv.nx, a.lv.ny, a.lv.plain_lo, a.lv.plain_hi) == 0) {
+      if (zp) fwd_tile<R, MODE, OPK, 0, true, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
+      else fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
+    } else {
+      fwd_tile<R, MODE, OPK, 2, true, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
     }
   }
 }

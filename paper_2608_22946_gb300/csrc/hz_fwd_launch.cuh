@@ -61,10 +61,10 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
   f.px1 = px1;
   f.py0 = py0;
   f.py1 = py1;
-  f.nwx = cdiv_i(nx, ShWide::TWN);
+  f.nwx = cdiv_i(px1 - px0 + 1, ShWide::TWN);
   f.nw_lo = cdiv_i(py0, ShWide::TYT);
   f.nw_hi = cdiv_i(ny - 1 - py1, ShWide::TYT);
-  f.nty = cdiv_i(py1 - py0 + 1, ShTall::TYT);
+  f.nty = cdiv_i(ny, ShTall::TYT);
   f.nt_lo = cdiv_i(px0, ShTall::TWN);
   f.nt_hi = cdiv_i(nx - 1 - px1, ShTall::TWN);
   f.count = f.nwx * (f.nw_lo + f.nw_hi) + f.nty * (f.nt_lo + f.nt_hi);
@@ -78,12 +78,15 @@ inline FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, bool ab) {
 }
 
 template <class R, int MODE, int OPK, int RB>
+void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nblk_total, cudaStream_t s);
+
+template <class R, int MODE, int OPK, int RB>
 void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
   const LevelView<R>& L = c.lv;
   const FwdPlan p = plan_fwd(L, c.nrhs, OPK != OPK_Q);
   const int ng = c.nrhs / RB;
   const int nblk_total = (int)p.blocks();
-  if (!p.split) {
+  if (OPK == OPK_Q || !p.split) {
     TileMap tm;
     tm.ntx = p.GW;
     tm.nblk_total = nblk_total;
@@ -92,6 +95,12 @@ void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
         c, p.zb, tm);
     return;
   }
+  if constexpr (OPK != OPK_Q) launch_fwd_split<R, MODE, OPK, RB>(c, p, ng, nblk_total, s);
+}
+
+// the rectangle and frame launches of a split application
+template <class R, int MODE, int OPK, int RB>
+void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nblk_total, cudaStream_t s) {
   TileMap ti;
   ti.ox = p.frame.px0;
   ti.oy = p.frame.py0;

@@ -331,7 +331,7 @@ long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock) {
 // and its block id for fused reductions).  Violations counted: a written
 // column outside the grid, a column outside the PML-free range on a row form
 // that drops that axis's PML corrections (form 0 both axes, form 1 y, form 3
-// x), a block id out of range or repeated.  counts (nx * ny * nz bytes, or
+// x), a block id out of range or repeated.  (The kernels use forms 0, 2, 3.)  counts (nx * ny * nz bytes, or
 // null) receives how often each node of right-hand side 0 is written,
 // saturating at 255.
 long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs, int zblock,
@@ -391,12 +391,10 @@ long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* p
       for (int t = 0; t < p.frame.count; ++t) {
         const FrameTile f = decode_frame(p.frame, t);
         const long long bid = off + t + (long long)p.frame.count * bz;
-        if (f.wide) {
-          const bool xplain = f.x0 >= plo[0] && f.x0 + ShWide::TWN - 1 <= phi[0];
-          cta(ShWide::NPX, ShWide::TXT, ShWide::TYT, f.x0, f.y0, f.rx1, f.ry1, xplain ? 3 : 2, p.zbf, bz, bid);
-        } else {
-          cta(ShTall::NPX, ShTall::TXT, ShTall::TYT, f.x0, f.y0, f.rx1, f.ry1, 1, p.zbf, bz, bid);
-        }
+        if (f.wide)
+          cta(ShWide::NPX, ShWide::TXT, ShWide::TYT, f.x0, f.y0, f.rx1, f.ry1, 3, p.zbf, bz, bid);
+        else
+          cta(ShTall::NPX, ShTall::TXT, ShTall::TYT, f.x0, f.y0, f.rx1, f.ry1, 2, p.zbf, bz, bid);
       }
   }
   for (unsigned char v : seen)
