@@ -141,11 +141,12 @@ hz_status hz_workspace_bytes(const hz_grid* grid, const hz_params* params, int m
 /* Replace the solver parameters (e.g. tolerance); cached CUDA graphs are dropped. */
 hz_status hz_set_params(hz_handle* h, const hz_params* params);
 
-/* Host-only check of the forward stencil's launch layout; no GPU work and no
- * counterpart in the paper.  Replays, for level `level` of `grid` (the same
- * checks as hz_create), how one forward application of op (HZ_OP_A, HZ_OP_B,
- * or HZ_OP_Q on level 0) with nrhs right-hand sides and the given z-blocks
- * (0: the built-in heuristic; zblock_f: the PML-frame launch, 0 = zblock)
+/* Host-only check of a stencil application's launch layout; no GPU work and
+ * no counterpart in the paper.  Replays, for level `level` of `grid` (the same
+ * checks as hz_create), how one application of op (forward: HZ_OP_A,
+ * HZ_OP_B, or HZ_OP_Q on level 0; adjoint: HZ_OP_A_ADJ, HZ_OP_B_ADJ) with
+ * nrhs right-hand sides and the given z-blocks (0: the built-in heuristic;
+ * zblock_f: the PML-frame launch of a forward application, 0 = zblock)
  * assigns grid nodes to CUDA blocks and threads.
  *   counts_host  HOST, N_L bytes, or NULL: times each node of right-hand side 0
  *                is written (saturating at 255; 1 everywhere is an exact cover).
@@ -184,8 +185,9 @@ hz_status iofd_apply(hz_handle* h, int level, int op, int precision, const void*
  *   g_dev, x_dev   DEVICE inputs, r_dev DEVICE output (N_L * nrhs, `precision`);
  *                  r must not alias g or x.
  *   norm2_dev      DEVICE double, nrhs values out.
- * Limits: nrhs <= 64 and (stencil blocks per rhs) * nrhs <= 65536; larger
- * problems return HZ_EINVAL with a message.  The first call on a device looks
+ * Limits: nrhs <= 64 and (blocks per rhs of the launch that runs -- forward
+ * or adjoint, which tile differently; hz_layout_check reports both) * nrhs
+ * <= 65536; larger problems return HZ_EINVAL with a message.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) and should come before
  * any stream capture.  Every call shares the one array: calls that overlap on
  * the GPU (concurrent streams, several handles) race and must be serialised. */

@@ -194,6 +194,8 @@ class Solver:
         import torch
         prec = HZ_C64 if x.dtype == torch.complex64 else HZ_C128
         n = self.N[level]
+        if x.numel() % n:
+            raise ValueError(f"x: {x.numel()} elements is not a whole number of level-{level} fields ({n})")
         nrhs = x.numel() // n
         _check_field(x, x.dtype, n * nrhs, "x")
         y = torch.empty_like(x) if out is None else out
@@ -210,11 +212,17 @@ class Solver:
         import torch
         prec = HZ_C64 if x.dtype == torch.complex64 else HZ_C128
         n = self.N[level]
+        if x.numel() % n:
+            raise ValueError(f"x: {x.numel()} elements is not a whole number of level-{level} fields ({n})")
         nrhs = x.numel() // n
         _check_field(x, x.dtype, n * nrhs, "x")
         _check_field(g, x.dtype, n * nrhs, "g")
         r = torch.empty_like(x) if out is None else out
-        n2 = torch.empty(nrhs, dtype=torch.float64, device="cuda") if norm2_out is None else norm2_out
+        _check_field(r, x.dtype, n * nrhs, "out")
+        n2 = torch.empty(nrhs, dtype=torch.float64, device=x.device) if norm2_out is None else norm2_out
+        if not (isinstance(n2, torch.Tensor) and n2.is_cuda and n2.dtype == torch.float64 and n2.is_contiguous()
+                and n2.numel() >= nrhs):
+            raise ValueError(f"norm2_out: need a contiguous CUDA float64 tensor with at least {nrhs} elements")
         self._ok(self._lib.iofd_residual_static(self._h, level, op, prec, ctypes.c_void_p(g.data_ptr()),
                                                 ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
                                                 ctypes.c_void_p(n2.data_ptr()), nrhs, _stream_ptr(stream)))

@@ -65,6 +65,7 @@ long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
 // Host replay of a forward stencil application's launch layout on a grid of
 // nx x ny x nz nodes: per-node write counts of right-hand side 0 (or null) and
 // the number of layout violations (defined beside the tiling).
+long long replay_adj_layout(int nx, int ny, int nz, int nrhs, int zblock, unsigned char* counts, long long* blocks);
 long long replay_fwd_layout(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int op, int nrhs,
                             int zblock, int zblock_f, unsigned char* counts, long long* blocks);
 

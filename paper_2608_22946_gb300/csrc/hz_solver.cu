@@ -1233,14 +1233,18 @@ hz_status hz_layout_check(const hz_grid* grid, int level, int op, int nrhs, int 
   hz_status st = run_guarded(&tmp, [&] {
     check_grid(*grid);
     HZ_REQUIRE(level >= 0 && level <= 2, "level must be 0, 1 or 2");
-    HZ_REQUIRE(op == HZ_OP_A || op == HZ_OP_B || op == HZ_OP_Q, "op must be HZ_OP_A, HZ_OP_B or HZ_OP_Q");
+    HZ_REQUIRE(op == HZ_OP_A || op == HZ_OP_B || op == HZ_OP_Q || op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ,
+               "op must be HZ_OP_A, HZ_OP_B, HZ_OP_Q, HZ_OP_A_ADJ or HZ_OP_B_ADJ");
     HZ_REQUIRE(op != HZ_OP_Q || level == 0, "Q_h is defined on the fine level only");
     HZ_REQUIRE(nrhs >= 1 && zblock >= 0 && zblock_f >= 0, "nrhs must be >= 1, z-blocks >= 0");
     Level lv;
     level_dims(*grid, level, lv);
     if (counts_host) std::memset(counts_host, 0, (size_t)lv.N);
-    *violations = replay_fwd_layout(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, op == HZ_OP_Q ? OP_Q : OP_AB,
-                                    nrhs, zblock, zblock_f, counts_host, blocks);
+    if (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ)
+      *violations = replay_adj_layout(lv.nx, lv.ny, lv.nz, nrhs, zblock, counts_host, blocks);
+    else
+      *violations = replay_fwd_layout(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, op == HZ_OP_Q ? OP_Q : OP_AB,
+                                      nrhs, zblock, zblock_f, counts_host, blocks);
   });
   g_create_error = tmp.err;
   return st;

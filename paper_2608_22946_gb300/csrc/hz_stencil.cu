@@ -402,6 +402,28 @@ long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* p
   return bad;
 }
 
+// Host replay of the adjoint launch layout (32 x 8 tiles over the whole grid,
+// adj_zblock planes per block unless zblock > 0): per-node write counts of
+// right-hand side 0 (or null) and the blocks per right-hand side.
+long long replay_adj_layout(int nx, int ny, int nz, int nrhs, int zblock, unsigned char* counts, long long* blocks) {
+  const int zb = zblock > 0 ? zblock : adj_zblock(nx, ny, nz, nrhs);
+  const int tx = (nx + TX - 1) / TX, ty = (ny + TY - 1) / TY, tz = (nz + zb - 1) / zb;
+  if (blocks) *blocks = (long long)tx * ty * tz;
+  if (counts)
+    for (int bz = 0; bz < tz; ++bz)
+      for (int by = 0; by < ty; ++by)
+        for (int bx = 0; bx < tx; ++bx)
+          for (int t = 0; t < NT; ++t) {
+            const int gx = bx * TX + t % TX, gy = by * TY + t / TX;
+            if (gx >= nx || gy >= ny) continue;
+            for (int z = bz * zb; z < std::min(bz * zb + zb, nz); ++z) {
+              unsigned char& c = counts[((size_t)z * ny + gy) * nx + gx];
+              if (c < 255) ++c;
+            }
+          }
+  return 0;
+}
+
 template <class R, int MODE, int OP>
 static void set_adj_attr() {
   constexpr int NP = AdjNP<OP>::v;

@@ -129,7 +129,7 @@ def test_forward_launch_layout_is_an_exact_cover(lib):
 
 def test_layout_check_validates_arguments(lib):
     import paper_2608_22946_gb300 as hz
-    for kw in [dict(level=3), dict(op=hz.HZ_OP_A_ADJ), dict(op=hz.HZ_OP_Q, level=1), dict(nrhs=0),
+    for kw in [dict(level=3), dict(op=hz.HZ_OP_Q_ADJ), dict(op=hz.HZ_OP_Q, level=1), dict(nrhs=0),
                dict(zblock=-1)]:
         with pytest.raises(hz.HzError) as e:
             hz.layout_check(48, 8, **kw)
@@ -183,3 +183,24 @@ def test_reduction_slots_are_sized_by_the_smallest_zblock(lib):
                     for zbf in (0, 4, 8, 22, 64):
                         _, b, bad = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=zb, zblock_f=zbf)
                         assert bad == 0 and b <= worst, (shape, lev, nrhs, zb, zbf, b, worst)
+
+
+def test_adjoint_launch_layout_and_partial_sums(lib):
+    """The adjoint stencil tiles the whole grid with 32 x 8 columns, each node
+    once.  On non-cubic grids its block count can exceed the forward one at the
+    same z-block (914 x 563 x 76 nodes at z-block 4: more adjoint blocks), so a
+    fused adjoint residual must be sized from its own launch; the handle's
+    partial-sum array covers both at the smallest z-block."""
+    import paper_2608_22946_gb300 as hz
+    grid = (916, 564, 76)   # intervals (917 x 565 x 77 nodes on level 0)
+    counts, adj, bad = hz.layout_check(grid, 12, level=0, op=hz.HZ_OP_A_ADJ, nrhs=16, zblock=4)
+    assert bad == 0 and counts.min() == 1 and counts.max() == 1
+    _, fwd, _ = hz.layout_check(grid, 12, level=0, op=hz.HZ_OP_A, nrhs=16, zblock=4, zblock_f=4)
+    assert adj > fwd, (adj, fwd)
+    for shape, p in [((288, 288, 288), 16), ((916, 564, 76), 12), ((40, 200, 24), 4), ((48, 48, 48), 8)]:
+        for lev in (0, 1, 2):
+            _, worst_f, _ = hz.layout_check(shape, p, level=lev, nrhs=1, zblock=4, zblock_f=4)
+            _, worst_a, _ = hz.layout_check(shape, p, level=lev, op=hz.HZ_OP_A_ADJ, nrhs=1, zblock=4)
+            for nrhs in (1, 3, 16):
+                _, a, _ = hz.layout_check(shape, p, level=lev, op=hz.HZ_OP_B_ADJ, nrhs=nrhs)
+                assert a <= max(worst_f, worst_a), (shape, lev, nrhs, a)

@@ -53,3 +53,43 @@ def test_static_residual_rejects_too_many_rhs(solver):
     with pytest.raises(hz.HzError) as e:
         s.residual_static(x, x.clone(), op=hz.HZ_OP_A, level=0)
     assert e.value.status == hz.HZ_EINVAL
+
+
+@pytest.mark.parametrize("opname", ["A", "A_ADJ"])
+def test_static_residual_on_the_split_layout(opname):
+    """A grid of more than 2^20 nodes runs the forward operator as two launches
+    (PML-free rectangle and PML frame, the frame on the handle's second stream);
+    both add their block sums to the one static array.  The adjoint tiles the
+    grid differently and sizes its own partial sums."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_22946_gb300 as hz
+    w = W.layered_inclusion(n=104, n_pml=8, nsrc=1)
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=1)
+    op = getattr(hz, "HZ_OP_" + opname)
+    shape = (1,) + s.level_shape[0]
+    for call in range(2):
+        g = torch.from_numpy(W.random_complex(shape, 30 + call)).to("cuda", torch.complex64)
+        x = torch.from_numpy(W.random_complex(shape, 40 + call)).to("cuda", torch.complex64)
+        r, n2 = s.residual_static(g, x, op=op, level=0)
+        r_ref = (g - s.iofd_apply(x, op=op, level=0)).to(torch.complex128)
+        err = float(torch.linalg.vector_norm(r.to(torch.complex128) - r_ref) / torch.linalg.vector_norm(r_ref))
+        assert err <= 1e-5, (call, err)
+        ref2 = float((r_ref.abs() ** 2).sum())
+        assert abs(float(n2[0]) / ref2 - 1) <= 1e-4, (call, float(n2[0]), ref2)
+    s.close()
+
+
+def test_static_residual_rejects_more_than_64_rhs():
+    """The static array holds arrival counters for 64 right-hand sides: a call
+    with 65 is refused before any launch, even on a handle sized for more."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_22946_gb300 as hz
+    w = W.homogeneous(n=8, n_pml=0)
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=65)
+    x = torch.zeros((65,) + s.level_shape[0], dtype=torch.complex64, device="cuda")
+    with pytest.raises(hz.HzError) as e:
+        s.residual_static(x, x.clone(), op=hz.HZ_OP_A, level=0)
+    assert e.value.status == hz.HZ_EINVAL and "64" in str(e.value)
+    s.close()
