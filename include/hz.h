@@ -96,6 +96,11 @@ typedef struct {
   int autotune;        /* nonzero: hz_create times the forward stencil on every level for a
                           set of z-block sizes (planes per thread block) and keeps the
                           fastest; zero: a fixed heuristic */
+  int refine;          /* HZ_C64 only.  1: FP64 iterative refinement around complex64
+                          corrections, each FP64 true residual deciding convergence
+                          (default).  0: the paper's protocol (Sec. 5.2, Table 4): one
+                          complex64 FGMRES(m_out) solve stopped by its own complex64 true
+                          residual at tol, no refinement pass; rel_res is that residual */
 } hz_params;
 
 typedef struct {
@@ -115,7 +120,7 @@ typedef struct hz_handle hz_handle;
 
 /* Table 4 defaults (Sec. 6.1): m_out 5, m_h 2 / nJ_h 2 / w_h 0.8, c_2h 2,
  * m_2h 10, nJ_2h 2 / w_2h 0.8, m_4h 4 / nJ_4h 2 / w_4h 0.2, sigma 0.9,
- * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8, autotune 1. */
+ * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8, autotune 1, refine 1. */
 void hz_default_params(hz_params* p);
 
 /* Create a solver for one frequency and velocity model.
@@ -172,6 +177,17 @@ hz_status iofd_coeffs(hz_handle* h, int level, double* kappa_dev, double* shell_
  * HZ_OP_Q / HZ_OP_Q_ADJ require level 0.  1 <= nrhs <= max_nrhs. */
 hz_status iofd_apply(hz_handle* h, int level, int op, int precision, const void* x_dev, void* y_dev, int nrhs,
                      void* stream);
+
+/* y = J_nsweeps(H, g; omega): the weighted Jacobi map from zero of
+ * Eq. jacobi-map, the smoother inside S_h (level 0, H = A_h) and inside the
+ * shifted cycle V_2h^sigma and the bottom solve C_4h (levels 1 and 2, H =
+ * B_ell), with the operator's own diagonal D: y_1 = omega D^-1 g and, for two
+ * sweeps, y = y_1 + omega D^-1 (g - H y_1).
+ *   op             HZ_OP_A on level 0, HZ_OP_B on levels 1 and 2.
+ *   nsweeps        1 or 2 (Table 4 uses 2 on every level).
+ *   g_dev, y_dev   DEVICE, N_L * nrhs in `precision`; distinct. */
+hz_status iofd_jacobi(hz_handle* h, int level, int op, int precision, int nsweeps, double omega, const void* g_dev,
+                      void* y_dev, int nrhs, void* stream);
 
 /* r = g - Op x and norm2[k] = ||r_k||^2 for each right-hand side k, without
  * allocating device memory during the call.  The paper has no counterpart:

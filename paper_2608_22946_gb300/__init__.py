@@ -24,7 +24,8 @@ _STATUS = {0: "HZ_OK", 1: "HZ_EINVAL", 2: "HZ_ENOMEM", 3: "HZ_ECUDA", 4: "HZ_ENO
 
 EXPORTED = ["hz_default_params", "hz_create", "hz_destroy", "hz_last_error", "hz_workspace_bytes",
             "hz_set_params", "iofd_coeffs", "iofd_apply", "threegrid_precond", "helmholtz_solve",
-            "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static", "hz_layout_check"]
+            "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static", "hz_layout_check",
+            "iofd_jacobi"]
 
 
 class HzGrid(ctypes.Structure):
@@ -43,7 +44,7 @@ class HzParams(ctypes.Structure):
                 ("nJ_2h", ctypes.c_int), ("m_4h", ctypes.c_int), ("nJ_4h", ctypes.c_int),
                 ("w_h", ctypes.c_double), ("w_2h", ctypes.c_double), ("w_4h", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("autotune", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hz_kernel_launches.restype = ctypes.c_ulonglong
     lib.iofd_coeffs.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.iofd_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
+    lib.iofd_jacobi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp,
+                                ctypes.c_int, vp]
     lib.iofd_residual_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                          ctypes.c_int, vp]
     lib.hz_layout_check.argtypes = [P(HzGrid), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -202,6 +205,27 @@ class Solver:
         _check_field(y, x.dtype, n * nrhs, "out")
         self._ok(self._lib.iofd_apply(self._h, level, op, prec, ctypes.c_void_p(x.data_ptr()),
                                       ctypes.c_void_p(y.data_ptr()), nrhs, _stream_ptr(stream)))
+        return y
+
+    # -- iofd_jacobi -----------------------------------------------------------
+    def iofd_jacobi(self, g, level=0, nsweeps=2, omega=None, out=None, stream=None):
+        """y = J_nsweeps(H, g; omega) with H = A_h on level 0 and B on levels 1, 2
+        (the smoothers of Algorithm 1); omega defaults to the handle's weight of
+        that level."""
+        import torch
+        prec = HZ_C64 if g.dtype == torch.complex64 else HZ_C128
+        n = self.N[level]
+        if g.numel() % n:
+            raise ValueError(f"g: {g.numel()} elements is not a whole number of level-{level} fields ({n})")
+        nrhs = g.numel() // n
+        _check_field(g, g.dtype, n * nrhs, "g")
+        y = torch.empty_like(g) if out is None else out
+        _check_field(y, g.dtype, n * nrhs, "out")
+        if omega is None:
+            omega = (self.params.w_h, self.params.w_2h, self.params.w_4h)[level]
+        op = HZ_OP_A if level == 0 else HZ_OP_B
+        self._ok(self._lib.iofd_jacobi(self._h, level, op, prec, nsweeps, float(omega), ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(y.data_ptr()), nrhs, _stream_ptr(stream)))
         return y
 
     # -- iofd_residual_static --------------------------------------------------

@@ -1074,6 +1074,25 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     return o;
   }
   ensure_work<float>(H);
+  if (!p.refine) {
+    // the paper's protocol: one complex64 FGMRES solve of the scaled system to
+    // tol, stopped by its complex64 true residual; v = ||b|| x64
+    std::vector<double> inv(nrhs), one(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+      inv[r] = bn[r] > 1e-300 ? 1.0 / bn[r] : 0.0;
+      one[r] = bn[r] > 0 ? 1.0 : 0.0;
+    }
+    HZ_CK(cudaMemcpyAsync(H->s_inv, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, H->st));
+    HZ_CK(cudaMemcpyAsync(H->s_root, bn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, H->st));
+    launch_c128_to_c64_scaled(b, H->b64, H->s_inv, (int)N, nrhs, H->st);
+    launch_zero<float>(H->x64, N * nrhs, H->st);
+    HZ_LAUNCHED();
+    o.rel = outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, p.tol, p.max_pc, o.pc);
+    launch_add_c64_to_c128_scaled(H->x64, x, H->s_root, (int)N, nrhs, H->st);
+    HZ_LAUNCHED();
+    HZ_CK(cudaStreamSynchronize(H->st));
+    return o;
+  }
   // FP64 iterative refinement around complex64 corrections
   bool x_zero = true;  // the initial guess: its residual is b, whose norms are known
   std::vector<double> root(nrhs), inv(nrhs);
@@ -1204,6 +1223,7 @@ void hz_default_params(hz_params* p) {
   p->inner_tol = 1e-5;
   p->max_refine = 8;
   p->autotune = 1;
+  p->refine = 1;
 }
 
 const char* hz_last_error(const hz_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -1429,6 +1449,34 @@ hz_status iofd_apply(hz_handle* H, int level, int op, int precision, const void*
         launch_stencil<double>(c, M_APPLY, isq ? OP_Q : OP_AB, adj, H->st);
       }
       HZ_LAUNCHED();
+    } catch (...) {
+      H->st = old;
+      throw;
+    }
+    H->st = old;
+  });
+}
+
+hz_status iofd_jacobi(hz_handle* H, int level, int op, int precision, int nsweeps, double omega, const void* g,
+                      void* y, int nrhs, void* stream) {
+  if (!H) return HZ_EINVAL;
+  return run_guarded(H, [&] {
+    HZ_REQUIRE(level >= 0 && level <= 2, "level must be 0, 1 or 2");
+    HZ_REQUIRE(op == (level == 0 ? HZ_OP_A : HZ_OP_B),
+               "the Jacobi maps of Algorithm 1 smooth A_h on level 0 and B on levels 1 and 2");
+    HZ_REQUIRE(nsweeps == 1 || nsweeps == 2, "nsweeps must be 1 or 2");
+    HZ_REQUIRE(g && y && g != y, "g and y must be distinct non-null device pointers");
+    HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
+    HZ_REQUIRE(precision == HZ_C64 || precision == HZ_C128, "precision must be HZ_C64 or HZ_C128");
+    cudaStream_t old = H->st;
+    H->st = (cudaStream_t)stream;
+    try {
+      if (precision == HZ_C64) {
+        jacobi<float>(H, level, level != 0, false, (const cx<float>*)g, (cx<float>*)y, nsweeps, omega, nrhs);
+      } else {
+        prepare_dinv_double(H);
+        jacobi<double>(H, level, level != 0, false, (const cx<double>*)g, (cx<double>*)y, nsweeps, omega, nrhs);
+      }
     } catch (...) {
       H->st = old;
       throw;

@@ -28,7 +28,9 @@ def _worker(rank, world, port, out):
     bench.barrier(pg)
     t_rank = 0.5 + rank          # rank 1 is the slowest
     t_max = bench.allreduce_max(pg, t_rank)
-    out[rank] = (t_max, bench.aggregate_rate(100.0, w, t_max))
+    units = bench.allreduce_sum(pg, 100.0 * (rank + 1))   # ranks process 100 and 200 units
+    srcs, scaling = bench.rank_sources(list(range(5)), "each", w, rank)
+    out[rank] = (t_max, bench.aggregate_rate(units, t_max), srcs, scaling)
     bench.barrier(pg)
     dist.destroy_process_group()
 
@@ -40,9 +42,11 @@ def test_two_rank_max_time_and_aggregate():
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
-        t_max, rate = out[r]
+        t_max, rate, srcs, scaling = out[r]
         assert t_max == 1.5
-        assert rate == pytest.approx(100.0 * 2 / 1.5)
+        assert rate == pytest.approx(300.0 / 1.5)
+        assert scaling == "strong"
+    assert out[0][2] + out[1][2] == list(range(5))   # the sources are split, each solved once
 
 
 def test_single_process_defaults(monkeypatch):
@@ -52,7 +56,9 @@ def test_single_process_defaults(monkeypatch):
     w, r, local, pg = bench.dist_setup(1)
     assert (w, r, pg) == (1, 0, None)
     assert bench.allreduce_max(pg, 3.0) == 3.0
-    assert bench.aggregate_rate(10.0, 1, 2.0) == 5.0
+    assert bench.aggregate_rate(10.0, 2.0) == 5.0
+    assert bench.rank_sources([1, 2, 3], "batch", 1, 0) == ([1, 2, 3], "weak")
+    assert bench.rank_sources([7], "one", 4, 3) == ([7], "weak")   # one source: every replica solves it
 
 
 def test_clock_summary_parses_samples_and_reasons():
@@ -80,11 +86,13 @@ def test_named_workloads_and_l2_note():
     """Each named bench workload builds with its stated grid and batch; the
     numeric aliases name the same workloads; the L2 note matches the sizes."""
     import bench
-    for name, (n, nrhs) in {"homogeneous_48": (48, 1), "gaussian_lens_288": (288, 1),
-                            "layered_inclusion_224x16": (224, 16)}.items():
-        w, sources, k, desc = bench.resolve_workload(name)
-        assert (w.n, k, len(sources)) == (n, nrhs, nrhs) and desc
+    for name, (n, nrhs, nsrc) in {"homogeneous_48": (48, 1, 1), "gaussian_lens_288": (288, 1, 1),
+                                  "layered_inclusion_224x16": (224, 16, 16)}.items():
+        w, sources, k, how, desc = bench.resolve_workload(name)
+        assert (w.n, k, len(sources)) == (n, nrhs, nsrc) and desc
         assert name.startswith(w.name)
+    gen, how, desc = bench.WORKLOADS["geophysical_960x4"]
+    assert (gen, how) == ("geophysical", "each")
     assert set(bench.CONFIG_ALIAS.values()) == set(bench.WORKLOADS)
     assert bench.l2_note(289 ** 3, 1).startswith("inputs larger than L2 (each fine complex64 field set 193 MB")
     assert bench.l2_note(49 ** 3, 1).startswith("inputs smaller than L2")
@@ -143,3 +151,59 @@ def test_reference_arm_other_ranks_exit_quietly():
                          env=dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
     assert out.returncode == 0 and out.stdout.strip() == ""
     assert time.perf_counter() - t0 < 60
+
+
+def test_partition_covers_each_source_once():
+    from paper_2608_22946_gb300 import replicas
+    for n in (1, 4, 7, 16):
+        for world in range(1, n + 1):
+            parts = [replicas.partition(n, world, r) for r in range(world)]
+            assert parts[0][0] == 0 and parts[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))
+            sizes = [b - a for a, b in parts]
+            assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 1
+
+
+def _grad_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group(backend="gloo")
+    import hz_workloads as W
+    from oracle import gradient as og
+    from paper_2608_22946_gb300 import replicas
+    w = W.random_field(n=20, n_pml=4, nsrc=4, nrec_side=3)
+    d_obs = og.synthetic_data(w.c_true, w.n_pml, w.h, w.omega, w.sources, w.receivers)
+
+    def misfit_grad(src, d):
+        J, g, _ = og.misfit_and_gradient(w.c, w.n_pml, w.h, w.omega, src, w.receivers, d)
+        return J, torch.from_numpy(g)
+
+    J, g = replicas.sharded_misfit_gradient(misfit_grad, w.sources, d_obs, world, rank)
+    out[rank] = (J, g.numpy())
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_the_sources_and_sum_the_gradient(monkeypatch):
+    """Replica gradient: each of two gloo ranks evaluates the adjoint-state
+    misfit and gradient for half of the sources (the oracle stands in for the
+    per-rank solver here); one all-reduce gives every rank the misfit and the
+    gradient of all sources, equal to the single-process evaluation."""
+    import numpy as np
+    import hz_workloads as W
+    from oracle import gradient as og
+    # one BLAS thread per rank (the spawned ranks inherit it): a multithreaded
+    # BLAS in two spawned processes beside torch's own threads stalls here
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        monkeypatch.setenv(var, "1")
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_grad_worker, args=(world, port, out), nprocs=world, join=True)
+    w = W.random_field(n=20, n_pml=4, nsrc=4, nrec_side=3)
+    d_obs = og.synthetic_data(w.c_true, w.n_pml, w.h, w.omega, w.sources, w.receivers)
+    J_ref, g_ref, _ = og.misfit_and_gradient(w.c, w.n_pml, w.h, w.omega, w.sources, w.receivers, d_obs)
+    for r in range(world):
+        J, g = out[r]
+        assert J == pytest.approx(J_ref, rel=1e-12)
+        assert np.allclose(g, g_ref, rtol=1e-12, atol=1e-12 * np.abs(g_ref).max())

@@ -324,3 +324,20 @@ def test_edge_grids_precond_and_solve(hz, case):
     vref, Q = _oracle_solution(prob, src, tol=1e-11)
     assert rel_l2(v.cpu().numpy()[0], vref[0]) <= 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_jacobi_map_matches_oracle(pair, hz, prec):
+    """The Jacobi maps of Algorithm 1 (Eq. jacobi-map) through iofd_jacobi: one
+    and two weighted sweeps from zero with A_h on level 0 and B_2h, B_4h on
+    levels 1 and 2, every row against the oracle's sweeps."""
+    w, prob, s = pair
+    tol = 1e-12 if prec == "c128" else 1e-5
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    for L, omega in ((0, 0.8), (1, 0.8), (2, 0.2)):
+        O = iofd.operator_A(prob, L, 0.0 if L == 0 else 0.9)
+        g = W.random_complex((1,) + prob.levels[L].shape, 60 + L)
+        for nJ in (1, 2):
+            ref = tg.jacobi(O, g[0], omega, nJ)
+            y = s.iofd_jacobi(to_dev(g, dt), level=L, nsweeps=nJ, omega=omega).cpu().numpy()[0]
+            assert rel_l2(y, ref) <= tol, (L, nJ, prec, rel_l2(y, ref))
