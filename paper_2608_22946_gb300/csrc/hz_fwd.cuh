@@ -70,9 +70,26 @@ struct FShape {
   static constexpr int NSLOT = (PLN + NT - 1) / NT;
   static_assert(NPX_ == 1 || PWS % 2 == 0, "paired columns need 16-byte aligned halo rows");
 };
-using ShRect = FShape<2, 32, 8>;  // 64 x 8: the PML-free rectangle, whole small grids
-using ShWide = FShape<2, 32, 4>;  // 64 x 4: PML strips below and above the rectangle (all x)
-using ShTall = FShape<1, 4, 32>;  // 4 x 32: PML strips left and right of it (its y range)
+// Tile sets.  Fine grids (set 0): two x-adjacent columns per thread, 64 x 8
+// rectangle tiles and 64 x 4 strips below / above the rectangle.  Coarse grids
+// (set 1, few nodes per block: parallelism matters more than per-node work):
+// one column per thread, 32 x 8 and 32 x 4.  Both: 4 x 32 strips left / right.
+template <int SS>
+struct Shapes;
+template <>
+struct Shapes<0> {
+  using Rect = FShape<2, 32, 8>;
+  using Wide = FShape<2, 32, 4>;
+  using Tall = FShape<1, 4, 32>;
+};
+template <>
+struct Shapes<1> {
+  using Rect = FShape<1, 32, 8>;
+  using Wide = FShape<1, 32, 4>;
+  using Tall = FShape<1, 4, 32>;
+};
+// grids below this many nodes use the coarse tile set
+constexpr long long kCoarseNodes = 8LL << 20;
 
 // ring depth by precision, mode and right-hand sides per block; PREF = NSTG - 2
 // planes are in flight, and the stage of the previous plane stays readable
@@ -107,14 +124,15 @@ struct FLayout {
 // launch layout
 // ----------------------------------------------------------------------------
 // Which tiles a launch covers.  Rectangle / grid launches: tile (t, blockIdx.y)
-// has its origin at (ox + 64 t, oy + 8 blockIdx.y) and writes columns up to
+// has its origin at (ox + rw t, oy + rh blockIdx.y) and writes columns up to
 // (rx1, ry1).  Frame launches: the PML frame around the PML-free rectangle
-// [px0, px1] x [py0, py1], as rows of 64 x 4 tiles below and above it (its x
-// range; only y is stretched there) followed by columns of 4 x 32 tiles left
+// [px0, px1] x [py0, py1], as rows of ww x wh tiles below and above it (its x
+// range; only y is stretched there) followed by columns of tw x th tiles left
 // and right of it (all y; x and, in the corners, y stretched).  All launches
 // of one operator application share one block numbering (bid_offset,
 // nblk_total) so that a fused grid reduction spans them.
 struct TileMap {
+  int rw = 64, rh = 8, ww = 64, wh = 4, tw = 4, th = 32;  // rectangle, wide- and tall-strip tile sizes
   int ox = 0, oy = 0, ntx = 1, rx1 = 0, ry1 = 0;
   int nx = 0, ny = 0, px0 = 0, px1 = -1, py0 = 0, py1 = -1;
   int nwx = 0, nw_lo = 0, nw_hi = 0;  // 64 x 4 tiles per strip row; tile rows below / above
@@ -133,26 +151,26 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
   const int nw = m.nwx * (m.nw_lo + m.nw_hi);
   if (t < nw) {
     const int r = t / m.nwx, c = t - r * m.nwx;
-    f.x0 = m.px0 + c * ShWide::TWN;
+    f.x0 = m.px0 + c * m.ww;
     f.rx1 = m.px1;
     if (r < m.nw_lo) {
-      f.y0 = r * ShWide::TYT;
+      f.y0 = r * m.wh;
       f.ry1 = m.py0 - 1;
     } else {
-      f.y0 = m.py1 + 1 + (r - m.nw_lo) * ShWide::TYT;
+      f.y0 = m.py1 + 1 + (r - m.nw_lo) * m.wh;
       f.ry1 = m.ny - 1;
     }
     f.wide = true;
   } else {
     const int u = t - nw, per = m.nt_lo + m.nt_hi;
     const int r = u / per, c = u - r * per;
-    f.y0 = r * ShTall::TYT;
+    f.y0 = r * m.th;
     f.ry1 = m.ny - 1;
     if (c < m.nt_lo) {
-      f.x0 = c * ShTall::TWN;
+      f.x0 = c * m.tw;
       f.rx1 = m.px0 - 1;
     } else {
-      f.x0 = m.px1 + 1 + (c - m.nt_lo) * ShTall::TWN;
+      f.x0 = m.px1 + 1 + (c - m.nt_lo) * m.tw;
       f.rx1 = m.nx - 1;
     }
     f.wide = false;
@@ -161,9 +179,9 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
 }
 
 // Row form of a whole-grid tile: 0 shell (x and y outside the PML), 2 general.
-__host__ __device__ __forceinline__ int grid_tile_form(int x0, int y0, int nx, int ny, const int* plo,
-                                                      const int* phi) {
-  const int xe = min(x0 + ShRect::TWN - 1, nx - 1), ye = min(y0 + ShRect::TYT - 1, ny - 1);
+__host__ __device__ __forceinline__ int grid_tile_form(int x0, int y0, int tw, int th, int nx, int ny,
+                                                      const int* plo, const int* phi) {
+  const int xe = min(x0 + tw - 1, nx - 1), ye = min(y0 + th - 1, ny - 1);
   const bool px = x0 >= plo[0] && xe <= phi[0], py = y0 >= plo[1] && ye <= phi[1];
   return (px && py) ? 0 : 2;
 }
@@ -710,15 +728,17 @@ __device__ __forceinline__ bool block_in_zpml(const LevelView<R>& L, int zblock)
 // kernels
 // ----------------------------------------------------------------------------
 // resident blocks per SM the register allocation targets
-template <class R, int RB, int NT>
+template <class R, int RB, int NT, int NPX, int OPK>
 struct FMinB {
-  static constexpr int v = sizeof(R) == 8 ? 1 : (NT == 256 ? 2 : 4);
+  static constexpr int v = sizeof(R) == 8 ? 1 : (NT == 256 ? (NPX == 1 && RB == 1 && OPK != OPK_B ? 3 : 2) : 4);
 };
 
 // the PML-free rectangle (shell rows)
-template <class R, int MODE, int OPK, int RB>
-__global__ void __launch_bounds__(ShRect::NT, FMinB<R, RB, ShRect::NT>::v) k_fwd_rect(StencilCall<R> a, int zblock,
-                                                                                        TileMap tm) {
+template <class R, int MODE, int OPK, int RB, int SS>
+__global__ void __launch_bounds__(Shapes<SS>::Rect::NT,
+                                  FMinB<R, RB, Shapes<SS>::Rect::NT, Shapes<SS>::Rect::NPX, OPK>::v)
+    k_fwd_rect(StencilCall<R> a, int zblock, TileMap tm) {
+  using ShRect = typename Shapes<SS>::Rect;
   extern __shared__ __align__(16) unsigned char fsm[];
   const int ng = a.nrhs / RB;
   const int g = blockIdx.x % ng, t = blockIdx.x / ng;
@@ -733,9 +753,11 @@ __global__ void __launch_bounds__(ShRect::NT, FMinB<R, RB, ShRect::NT>::v) k_fwd
 
 // the PML frame around it: strips below and above the rectangle (y stretched)
 // and left and right of it (x stretched, y too in the corners)
-template <class R, int MODE, int OPK, int RB>
-__global__ void __launch_bounds__(ShWide::NT, FMinB<R, RB, ShWide::NT>::v) k_fwd_frame(StencilCall<R> a, int zblock,
-                                                                                         TileMap tm) {
+template <class R, int MODE, int OPK, int RB, int SS>
+__global__ void __launch_bounds__(Shapes<SS>::Wide::NT, FMinB<R, RB, Shapes<SS>::Wide::NT, 2, OPK>::v)
+    k_fwd_frame(StencilCall<R> a, int zblock, TileMap tm) {
+  using ShWide = typename Shapes<SS>::Wide;
+  using ShTall = typename Shapes<SS>::Tall;
   static_assert(ShWide::NT == ShTall::NT, "one block size for both frame tile shapes");
   extern __shared__ __align__(16) unsigned char fsm[];
   const int ng = a.nrhs / RB;
@@ -755,9 +777,10 @@ __global__ void __launch_bounds__(ShWide::NT, FMinB<R, RB, ShWide::NT>::v) k_fwd
 
 // a whole (small) grid in one launch, the row form chosen per tile; Q_h (shell
 // form everywhere) always takes this path
-template <class R, int MODE, int OPK, int RB>
-__global__ void __launch_bounds__(ShRect::NT, sizeof(R) == 8 ? 1 : 2) k_fwd_grid(StencilCall<R> a, int zblock,
-                                                                                  TileMap tm) {
+template <class R, int MODE, int OPK, int RB, int SS>
+__global__ void __launch_bounds__(Shapes<SS>::Rect::NT, sizeof(R) == 8 ? 1 : 2) k_fwd_grid(StencilCall<R> a, int zblock,
+                                                                                           TileMap tm) {
+  using ShRect = typename Shapes<SS>::Rect;
   extern __shared__ __align__(16) unsigned char fsm[];
   const int ng = a.nrhs / RB;
   const int g = blockIdx.x % ng, t = blockIdx.x / ng;
@@ -769,7 +792,7 @@ __global__ void __launch_bounds__(ShRect::NT, sizeof(R) == 8 ? 1 : 2) k_fwd_grid
     fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
   } else {
     const bool zp = block_in_zpml(a.lv, zblock);
-    if (grid_tile_form(x0, y0, a.lv.nx, a.lv.ny, a.lv.plain_lo, a.lv.plain_hi) == 0) {
+    if (grid_tile_form(x0, y0, ShRect::TWN, ShRect::TYT, a.lv.nx, a.lv.ny, a.lv.plain_lo, a.lv.plain_hi) == 0) {
       if (zp) fwd_tile<R, MODE, OPK, 0, true, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
       else fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
     } else {
@@ -778,11 +801,12 @@ __global__ void __launch_bounds__(ShRect::NT, sizeof(R) == 8 ? 1 : 2) k_fwd_grid
   }
 }
 
-template <class R, int MODE, int OPK, int RB>
-constexpr size_t fwd_smem_rect() { return FLayout<R, MODE, OPK, ShRect, RB>::bytes; }
-template <class R, int MODE, int OPK, int RB>
+template <class R, int MODE, int OPK, int RB, int SS>
+constexpr size_t fwd_smem_rect() { return FLayout<R, MODE, OPK, typename Shapes<SS>::Rect, RB>::bytes; }
+template <class R, int MODE, int OPK, int RB, int SS>
 constexpr size_t fwd_smem_frame() {
-  return std::max(FLayout<R, MODE, OPK, ShWide, RB>::bytes, FLayout<R, MODE, OPK, ShTall, RB>::bytes);
+  return std::max(FLayout<R, MODE, OPK, typename Shapes<SS>::Wide, RB>::bytes,
+                  FLayout<R, MODE, OPK, typename Shapes<SS>::Tall, RB>::bytes);
 }
 
 }  // namespace hz

@@ -7,11 +7,17 @@
 
 namespace hz {
 
+// tile set of a grid (hz_fwd.cuh)
+inline int tile_set(int nx, int ny, int nz) { return (long long)nx * ny * nz < kCoarseNodes ? 1 : 0; }
+inline int rect_w(int ss) { return ss ? Shapes<1>::Rect::TWN : Shapes<0>::Rect::TWN; }
+inline int rect_h(int ss) { return ss ? Shapes<1>::Rect::TYT : Shapes<0>::Rect::TYT; }
+
 // Planes per block when neither the caller nor the tuner chose: about four
 // waves of two blocks on 152 SMs, at least kMinZblock planes.
 inline int choose_zblock(int nx, int ny, int nz, int nrhs) {
+  const int ss = tile_set(nx, ny, nz);
   const long long tiles =
-      (long long)((nx + ShRect::TWN - 1) / ShRect::TWN) * ((ny + ShRect::TYT - 1) / ShRect::TYT) * nrhs;
+      (long long)((nx + rect_w(ss) - 1) / rect_w(ss)) * ((ny + rect_h(ss) - 1) / rect_h(ss)) * nrhs;
   const long long want = 152LL * 2 * 4;
   const long long nzb = (want + tiles - 1) / tiles;
   int zb = (int)((nz + nzb - 1) / nzb);
@@ -20,20 +26,19 @@ inline int choose_zblock(int nx, int ny, int nz, int nrhs) {
   return zb;
 }
 
-// Grids of at least this many nodes split the A/B application into the
-// PML-free rectangle and the PML frame (two launches, each carrying only its
-// own row forms' registers); smaller grids, where launch latency dominates,
-// use one launch that chooses the row form per tile.
-constexpr long long kSplitNodes = 1LL << 20;
-
 inline int cdiv_i(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
 
+// An A/B application with a PML-free core runs as two launches, the
+// PML-free rectangle (shell rows) and the PML frame around it, each carrying
+// only its own row forms (and run side by side on two streams); Q_h, and
+// grids whose PML leaves no core, use one launch choosing the form per tile.
 struct FwdPlan {
+  int ss = 0;             // tile set
   int zb = 4, nzb = 1;    // whole grid or rectangle
   int zbf = 4, nzbf = 1;  // frame
   bool split = false;
-  int GW = 1, GH = 1;     // whole-grid 64 x 8 tiles
-  int RW = 0, RH = 0;     // 64 x 8 tiles of the PML-free rectangle
+  int GW = 1, GH = 1;     // whole-grid tiles
+  int RW = 0, RH = 0;     // tiles of the PML-free rectangle
   TileMap frame;          // frame tiling (count = frame tiles per z-block)
   long long blocks() const {
     return split ? (long long)RW * RH * nzb + (long long)frame.count * nzbf : (long long)GW * GH * nzb;
@@ -46,27 +51,34 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
   p.nzb = (nz + p.zb - 1) / p.zb;
   p.zbf = std::min(std::min(zbf > 0 ? zbf : zb, kMaxZb), nz);
   p.nzbf = (nz + p.zbf - 1) / p.zbf;
-  p.GW = cdiv_i(nx, ShRect::TWN);
-  p.GH = cdiv_i(ny, ShRect::TYT);
+  p.ss = tile_set(nx, ny, nz);
+  TileMap& f = p.frame;
+  f.rw = rect_w(p.ss);
+  f.rh = rect_h(p.ss);
+  f.ww = p.ss ? Shapes<1>::Wide::TWN : Shapes<0>::Wide::TWN;
+  f.wh = p.ss ? Shapes<1>::Wide::TYT : Shapes<0>::Wide::TYT;
+  f.tw = Shapes<0>::Tall::TWN;
+  f.th = Shapes<0>::Tall::TYT;
+  p.GW = cdiv_i(nx, f.rw);
+  p.GH = cdiv_i(ny, f.rh);
   const int px0 = std::max(plo[0], 0), px1 = std::min(phi[0], nx - 1);
   const int py0 = std::max(plo[1], 0), py1 = std::min(phi[1], ny - 1);
-  p.split = ab && (long long)nx * ny * nz >= kSplitNodes && px1 >= px0 && py1 >= py0;
+  p.split = ab && px1 >= px0 && py1 >= py0;
   if (!p.split) return p;
-  p.RW = cdiv_i(px1 - px0 + 1, ShRect::TWN);
-  p.RH = cdiv_i(py1 - py0 + 1, ShRect::TYT);
-  TileMap& f = p.frame;
+  p.RW = cdiv_i(px1 - px0 + 1, f.rw);
+  p.RH = cdiv_i(py1 - py0 + 1, f.rh);
   f.nx = nx;
   f.ny = ny;
   f.px0 = px0;
   f.px1 = px1;
   f.py0 = py0;
   f.py1 = py1;
-  f.nwx = cdiv_i(px1 - px0 + 1, ShWide::TWN);
-  f.nw_lo = cdiv_i(py0, ShWide::TYT);
-  f.nw_hi = cdiv_i(ny - 1 - py1, ShWide::TYT);
-  f.nty = cdiv_i(ny, ShTall::TYT);
-  f.nt_lo = cdiv_i(px0, ShTall::TWN);
-  f.nt_hi = cdiv_i(nx - 1 - px1, ShTall::TWN);
+  f.nwx = cdiv_i(px1 - px0 + 1, f.ww);
+  f.nw_lo = cdiv_i(py0, f.wh);
+  f.nw_hi = cdiv_i(ny - 1 - py1, f.wh);
+  f.nty = cdiv_i(ny, f.th);
+  f.nt_lo = cdiv_i(px0, f.tw);
+  f.nt_hi = cdiv_i(nx - 1 - px1, f.tw);
   f.count = f.nwx * (f.nw_lo + f.nw_hi) + f.nty * (f.nt_lo + f.nt_hi);
   return p;
 }
@@ -77,31 +89,36 @@ inline FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, bool ab) {
   return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f);
 }
 
-template <class R, int MODE, int OPK, int RB>
+template <class R, int MODE, int OPK, int RB, int SS>
 void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nblk_total, cudaStream_t s);
 
-template <class R, int MODE, int OPK, int RB>
-void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
-  const LevelView<R>& L = c.lv;
-  const FwdPlan p = plan_fwd(L, c.nrhs, OPK != OPK_Q);
+template <class R, int MODE, int OPK, int RB, int SS>
+void launch_fwd_ss(const StencilCall<R>& c, const FwdPlan& p, cudaStream_t s) {
   const int ng = c.nrhs / RB;
   const int nblk_total = (int)p.blocks();
   if (OPK == OPK_Q || !p.split) {
-    TileMap tm;
+    TileMap tm = p.frame;
     tm.ntx = p.GW;
     tm.nblk_total = nblk_total;
     count_launch();
-    k_fwd_grid<R, MODE, OPK, RB><<<dim3(p.GW * ng, p.GH, p.nzb), ShRect::NT, fwd_smem_rect<R, MODE, OPK, RB>(), s>>>(
-        c, p.zb, tm);
+    k_fwd_grid<R, MODE, OPK, RB, SS><<<dim3(p.GW * ng, p.GH, p.nzb), Shapes<SS>::Rect::NT,
+                                       fwd_smem_rect<R, MODE, OPK, RB, SS>(), s>>>(c, p.zb, tm);
     return;
   }
-  if constexpr (OPK != OPK_Q) launch_fwd_split<R, MODE, OPK, RB>(c, p, ng, nblk_total, s);
+  if constexpr (OPK != OPK_Q) launch_fwd_split<R, MODE, OPK, RB, SS>(c, p, ng, nblk_total, s);
+}
+
+template <class R, int MODE, int OPK, int RB>
+void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
+  const FwdPlan p = plan_fwd(c.lv, c.nrhs, OPK != OPK_Q);
+  if (p.ss) launch_fwd_ss<R, MODE, OPK, RB, 1>(c, p, s);
+  else launch_fwd_ss<R, MODE, OPK, RB, 0>(c, p, s);
 }
 
 // the rectangle and frame launches of a split application
-template <class R, int MODE, int OPK, int RB>
+template <class R, int MODE, int OPK, int RB, int SS>
 void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nblk_total, cudaStream_t s) {
-  TileMap ti;
+  TileMap ti = p.frame;
   ti.ox = p.frame.px0;
   ti.oy = p.frame.py0;
   ti.ntx = p.RW;
@@ -121,12 +138,12 @@ void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nbl
     cudaStreamWaitEvent(s2, c.fork, 0);
   }
   count_launch();
-  k_fwd_rect<R, MODE, OPK, RB><<<dim3(p.RW * ng, p.RH, p.nzb), ShRect::NT, fwd_smem_rect<R, MODE, OPK, RB>(), s>>>(
-      c, p.zb, ti);
+  k_fwd_rect<R, MODE, OPK, RB, SS><<<dim3(p.RW * ng, p.RH, p.nzb), Shapes<SS>::Rect::NT,
+                                     fwd_smem_rect<R, MODE, OPK, RB, SS>(), s>>>(c, p.zb, ti);
   if (tp.count > 0) {
     count_launch();
-    k_fwd_frame<R, MODE, OPK, RB><<<dim3(tp.count * ng, 1, p.nzbf), ShWide::NT, fwd_smem_frame<R, MODE, OPK, RB>(),
-                                    s2>>>(c, p.zbf, tp);
+    k_fwd_frame<R, MODE, OPK, RB, SS><<<dim3(tp.count * ng, 1, p.nzbf), Shapes<SS>::Wide::NT,
+                                        fwd_smem_frame<R, MODE, OPK, RB, SS>(), s2>>>(c, p.zbf, tp);
   }
   if (fork) {
     cudaEventRecord(c.join, s2);
@@ -155,16 +172,21 @@ void launch_fwd_opk(const StencilCall<R>& c, cudaStream_t s) {
   launch_fwd_rb<R, MODE, OPK, 1>(c, s);
 }
 
+template <class R, int MODE, int OPK, int RB, int SS>
+void fwd_attrs_ss() {
+  cudaFuncSetAttribute(k_fwd_grid<R, MODE, OPK, RB, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fwd_smem_rect<R, MODE, OPK, RB, SS>());
+  if constexpr (OPK != OPK_Q) {
+    cudaFuncSetAttribute(k_fwd_rect<R, MODE, OPK, RB, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem_rect<R, MODE, OPK, RB, SS>());
+    cudaFuncSetAttribute(k_fwd_frame<R, MODE, OPK, RB, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem_frame<R, MODE, OPK, RB, SS>());
+  }
+}
 template <class R, int MODE, int OPK, int RB>
 void fwd_attrs_rb() {
-  cudaFuncSetAttribute(k_fwd_grid<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)fwd_smem_rect<R, MODE, OPK, RB>());
-  if constexpr (OPK != OPK_Q) {
-    cudaFuncSetAttribute(k_fwd_rect<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fwd_smem_rect<R, MODE, OPK, RB>());
-    cudaFuncSetAttribute(k_fwd_frame<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fwd_smem_frame<R, MODE, OPK, RB>());
-  }
+  fwd_attrs_ss<R, MODE, OPK, RB, 0>();
+  fwd_attrs_ss<R, MODE, OPK, RB, 1>();
 }
 template <class R, int MODE, int OPK>
 void fwd_attrs_opk() {

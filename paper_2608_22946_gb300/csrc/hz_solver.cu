@@ -837,8 +837,9 @@ void ensure_work(hz_handle* H) {
   if (sizeof(R) == sizeof(double)) prepare_dinv_double(H);
 }
 
-// Launch-shape autotuner: on every level, time the forward stencil (A_L apply,
-// nrhs = max_nrhs, the hierarchy's precision) for a set of z-block sizes on two
+// Launch-shape autotuner: on every level, time the forward stencil (the A_h
+// apply on the fine level, the Jacobi map of B on the coarse levels; nrhs =
+// max_nrhs, the hierarchy's precision) for a set of z-block sizes on two
 // workspace vectors and keep the fastest; where the level splits into the
 // PML-free rectangle and the PML frame, the frame's z-block is then tuned with
 // the rectangle's fixed.  Runs once, at creation.
@@ -890,16 +891,24 @@ void autotune_zblocks(hz_handle* H) {
     const long long n = lv.N * nr;
     launch_zero<R>(src[L], n, H->st);
     HZ_LAUNCHED();
+    // the launch each level runs most: the A_h apply on the fine level, the
+    // two-sweep Jacobi map of the shifted operator on the coarse levels
+    // (the V-cycle and the bottom solve)
+    const int mode = L == 0 ? M_APPLY : M_J2;
     auto time_apply = [&]() {
-      StencilCall<R> c = call<R>(H, L, false, nr);
+      StencilCall<R> c = call<R>(H, L, L > 0, nr);
       c.x = src[L];
       c.y = src[L] + n;  // the next basis vector of the same workspace
-      launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);  // warm-up
+      if (L > 0) {
+        c.dinv = Sel<R>::dinv(H->lev[L], true);
+        c.omega_j = (R)(L == 1 ? H->p.w_2h : H->p.w_4h);
+      }
+      launch_stencil<R>(c, mode, OP_AB, false, H->st);  // warm-up
       float ms = 0.f;
       // short launches (coarse levels) are timed over more repetitions
       for (int reps : {3, 24}) {
         HZ_CK(cudaEventRecord(e0, H->st));
-        for (int rep = 0; rep < reps; ++rep) launch_stencil<R>(c, M_APPLY, OP_AB, false, H->st);
+        for (int rep = 0; rep < reps; ++rep) launch_stencil<R>(c, mode, OP_AB, false, H->st);
         HZ_CK(cudaEventRecord(e1, H->st));
         HZ_LAUNCHED();
         HZ_CK(cudaEventSynchronize(e1));

@@ -370,31 +370,34 @@ long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* p
       }
     }
   };
+  const TileMap& m = p.frame;
+  const int rnpx = p.ss ? Shapes<1>::Rect::NPX : Shapes<0>::Rect::NPX;
+  const int wnpx = p.ss ? Shapes<1>::Wide::NPX : Shapes<0>::Wide::NPX;
+  const int tnpx = Shapes<0>::Tall::NPX;
   if (!p.split) {
     for (int bz = 0; bz < p.nzb; ++bz)
       for (int by = 0; by < p.GH; ++by)
         for (int t = 0; t < p.GW; ++t) {
-          const int x0 = t * ShRect::TWN, y0 = by * ShRect::TYT;
-          const int form = ab ? grid_tile_form(x0, y0, nx, ny, plo, phi) : 0;
-          cta(ShRect::NPX, ShRect::TXT, ShRect::TYT, x0, y0, nx - 1, ny - 1, form, p.zb, bz,
-              t + (long long)p.GW * (by + p.GH * bz));
+          const int x0 = t * m.rw, y0 = by * m.rh;
+          const int form = ab ? (grid_tile_form(x0, y0, m.rw, m.rh, nx, ny, plo, phi) == 0 ? 0 : 2) : 0;
+          cta(rnpx, m.rw / rnpx, m.rh, x0, y0, nx - 1, ny - 1, form, p.zb, bz, t + (long long)p.GW * (by + p.GH * bz));
         }
   } else {
     const int px0 = p.frame.px0, py0 = p.frame.py0;
     for (int bz = 0; bz < p.nzb; ++bz)
       for (int by = 0; by < p.RH; ++by)
         for (int t = 0; t < p.RW; ++t)
-          cta(ShRect::NPX, ShRect::TXT, ShRect::TYT, px0 + t * ShRect::TWN, py0 + by * ShRect::TYT, p.frame.px1,
-              p.frame.py1, 0, p.zb, bz, t + (long long)p.RW * (by + p.RH * bz));
+          cta(rnpx, m.rw / rnpx, m.rh, px0 + t * m.rw, py0 + by * m.rh, p.frame.px1, p.frame.py1, 0, p.zb, bz,
+              t + (long long)p.RW * (by + p.RH * bz));
     const long long off = (long long)p.RW * p.RH * p.nzb;
     for (int bz = 0; bz < p.nzbf; ++bz)
       for (int t = 0; t < p.frame.count; ++t) {
         const FrameTile f = decode_frame(p.frame, t);
         const long long bid = off + t + (long long)p.frame.count * bz;
         if (f.wide)
-          cta(ShWide::NPX, ShWide::TXT, ShWide::TYT, f.x0, f.y0, f.rx1, f.ry1, 3, p.zbf, bz, bid);
+          cta(wnpx, m.ww / wnpx, m.wh, f.x0, f.y0, f.rx1, f.ry1, 3, p.zbf, bz, bid);
         else
-          cta(ShTall::NPX, ShTall::TXT, ShTall::TYT, f.x0, f.y0, f.rx1, f.ry1, 2, p.zbf, bz, bid);
+          cta(tnpx, m.tw / tnpx, m.th, f.x0, f.y0, f.rx1, f.ry1, 2, p.zbf, bz, bid);
       }
   }
   for (unsigned char v : seen)
