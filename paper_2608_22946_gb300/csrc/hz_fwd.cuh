@@ -88,8 +88,17 @@ struct Shapes<1> {
   using Wide = FShape<1, 32, 4>;
   using Tall = FShape<1, 4, 32>;
 };
-// grids below this many nodes use the coarse tile set
+// Small grids (set 2): rectangle and frame tiles in ONE launch of 256-thread
+// blocks (launch latency dominates there): 32 x 8, 64 x 4 and 4 x 64.
+template <>
+struct Shapes<2> {
+  using Rect = FShape<1, 32, 8>;
+  using Wide = FShape<1, 64, 4>;
+  using Tall = FShape<1, 4, 64>;
+};
+// grids below this many nodes use the coarse tile set, below kFusedNodes the fused launch
 constexpr long long kCoarseNodes = 8LL << 20;
+constexpr long long kFusedNodes = 1LL << 20;
 
 // ring depth by precision, mode and right-hand sides per block; PREF = NSTG - 2
 // planes are in flight, and the stage of the previous plane stays readable
@@ -133,7 +142,7 @@ struct FLayout {
 // nblk_total) so that a fused grid reduction spans them.
 struct TileMap {
   int rw = 64, rh = 8, ww = 64, wh = 4, tw = 4, th = 32;  // rectangle, wide- and tall-strip tile sizes
-  int ox = 0, oy = 0, ntx = 1, rx1 = 0, ry1 = 0;
+  int ox = 0, oy = 0, ntx = 1, nrow = 1, rx1 = 0, ry1 = 0;
   int nx = 0, ny = 0, px0 = 0, px1 = -1, py0 = 0, py1 = -1;
   int nwx = 0, nw_lo = 0, nw_hi = 0;  // 64 x 4 tiles per strip row; tile rows below / above
   int nty = 0, nt_lo = 0, nt_hi = 0;  // rows of 4 x 32 tiles; tiles left / right per row
@@ -799,6 +808,43 @@ __global__ void __launch_bounds__(Shapes<SS>::Rect::NT, sizeof(R) == 8 ? 1 : 2) 
       fwd_tile<R, MODE, OPK, 2, true, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
     }
   }
+}
+
+// rectangle and frame tiles of a small grid in one launch (tile set 2): block t
+// < RW * RH (tm.ntx * tm.rows) is a rectangle tile, the rest frame tiles
+template <class R, int MODE, int OPK, int RB>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2) k_fwd_fused(StencilCall<R> a, int zblock, TileMap tm) {
+  using SRect = Shapes<2>::Rect;
+  using SWide = Shapes<2>::Wide;
+  using STall = Shapes<2>::Tall;
+  static_assert(SRect::NT == 256 && SWide::NT == 256 && STall::NT == 256, "one block size");
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int ng = a.nrhs / RB;
+  const int g = blockIdx.x % ng, t = blockIdx.x / ng;
+  const int nrect = tm.ntx * tm.nrow;
+  const unsigned bid = (unsigned)(t + (nrect + tm.count) * blockIdx.z);
+  const unsigned nb = (unsigned)tm.nblk_total;
+  const bool zp = block_in_zpml(a.lv, zblock);
+  if (t < nrect) {
+    const int x0 = tm.px0 + (t % tm.ntx) * SRect::TWN, y0 = tm.py0 + (t / tm.ntx) * SRect::TYT;
+    if (zp) fwd_tile<R, MODE, OPK, 0, true, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 0, false, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);
+    return;
+  }
+  const FrameTile f = decode_frame(tm, t - nrect);
+  if (f.wide) {
+    if (zp) fwd_tile<R, MODE, OPK, 3, true, SWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 3, false, SWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+  } else {
+    fwd_tile<R, MODE, OPK, 2, true, STall, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+  }
+}
+
+template <class R, int MODE, int OPK, int RB>
+constexpr size_t fwd_smem_fused() {
+  return std::max(std::max(FLayout<R, MODE, OPK, Shapes<2>::Rect, RB>::bytes,
+                           FLayout<R, MODE, OPK, Shapes<2>::Wide, RB>::bytes),
+                  FLayout<R, MODE, OPK, Shapes<2>::Tall, RB>::bytes);
 }
 
 template <class R, int MODE, int OPK, int RB, int SS>

@@ -8,7 +8,10 @@
 namespace hz {
 
 // tile set of a grid (hz_fwd.cuh)
-inline int tile_set(int nx, int ny, int nz) { return (long long)nx * ny * nz < kCoarseNodes ? 1 : 0; }
+inline int tile_set(int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz;
+  return n < kFusedNodes ? 2 : (n < kCoarseNodes ? 1 : 0);
+}
 inline int rect_w(int ss) { return ss ? Shapes<1>::Rect::TWN : Shapes<0>::Rect::TWN; }
 inline int rect_h(int ss) { return ss ? Shapes<1>::Rect::TYT : Shapes<0>::Rect::TYT; }
 
@@ -37,10 +40,12 @@ struct FwdPlan {
   int zb = 4, nzb = 1;    // whole grid or rectangle
   int zbf = 4, nzbf = 1;  // frame
   bool split = false;
+  bool fused = false;     // split tiles in one launch (tile set 2; one z-block)
   int GW = 1, GH = 1;     // whole-grid tiles
   int RW = 0, RH = 0;     // tiles of the PML-free rectangle
   TileMap frame;          // frame tiling (count = frame tiles per z-block)
   long long blocks() const {
+    if (fused) return ((long long)RW * RH + frame.count) * nzb;
     return split ? (long long)RW * RH * nzb + (long long)frame.count * nzbf : (long long)GW * GH * nzb;
   }
 };
@@ -55,10 +60,10 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
   TileMap& f = p.frame;
   f.rw = rect_w(p.ss);
   f.rh = rect_h(p.ss);
-  f.ww = p.ss ? Shapes<1>::Wide::TWN : Shapes<0>::Wide::TWN;
-  f.wh = p.ss ? Shapes<1>::Wide::TYT : Shapes<0>::Wide::TYT;
-  f.tw = Shapes<0>::Tall::TWN;
-  f.th = Shapes<0>::Tall::TYT;
+  f.ww = p.ss == 2 ? Shapes<2>::Wide::TWN : (p.ss ? Shapes<1>::Wide::TWN : Shapes<0>::Wide::TWN);
+  f.wh = p.ss == 2 ? Shapes<2>::Wide::TYT : (p.ss ? Shapes<1>::Wide::TYT : Shapes<0>::Wide::TYT);
+  f.tw = p.ss == 2 ? Shapes<2>::Tall::TWN : Shapes<0>::Tall::TWN;
+  f.th = p.ss == 2 ? Shapes<2>::Tall::TYT : Shapes<0>::Tall::TYT;
   p.GW = cdiv_i(nx, f.rw);
   p.GH = cdiv_i(ny, f.rh);
   const int px0 = std::max(plo[0], 0), px1 = std::min(phi[0], nx - 1);
@@ -80,6 +85,13 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
   f.nt_lo = cdiv_i(px0, f.tw);
   f.nt_hi = cdiv_i(nx - 1 - px1, f.tw);
   f.count = f.nwx * (f.nw_lo + f.nw_hi) + f.nty * (f.nt_lo + f.nt_hi);
+  f.ntx = p.RW;
+  f.nrow = p.RH;
+  if (p.ss == 2) {  // one launch, one z-block for every tile
+    p.fused = true;
+    p.zbf = p.zb;
+    p.nzbf = p.nzb;
+  }
   return p;
 }
 
@@ -111,8 +123,19 @@ void launch_fwd_ss(const StencilCall<R>& c, const FwdPlan& p, cudaStream_t s) {
 template <class R, int MODE, int OPK, int RB>
 void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
   const FwdPlan p = plan_fwd(c.lv, c.nrhs, OPK != OPK_Q);
-  if (p.ss) launch_fwd_ss<R, MODE, OPK, RB, 1>(c, p, s);
-  else launch_fwd_ss<R, MODE, OPK, RB, 0>(c, p, s);
+  if constexpr (OPK != OPK_Q) {
+    if (p.fused) {
+      TileMap tm = p.frame;
+      tm.nblk_total = (int)p.blocks();
+      const int ng = c.nrhs / RB;
+      count_launch();
+      k_fwd_fused<R, MODE, OPK, RB><<<dim3((p.RW * p.RH + tm.count) * ng, 1, p.nzb), 256,
+                                      fwd_smem_fused<R, MODE, OPK, RB>(), s>>>(c, p.zb, tm);
+      return;
+    }
+  }
+  if (p.ss == 0) launch_fwd_ss<R, MODE, OPK, RB, 0>(c, p, s);
+  else launch_fwd_ss<R, MODE, OPK, RB, 1>(c, p, s);
 }
 
 // the rectangle and frame launches of a split application
@@ -187,6 +210,9 @@ template <class R, int MODE, int OPK, int RB>
 void fwd_attrs_rb() {
   fwd_attrs_ss<R, MODE, OPK, RB, 0>();
   fwd_attrs_ss<R, MODE, OPK, RB, 1>();
+  if constexpr (OPK != OPK_Q)
+    cudaFuncSetAttribute(k_fwd_fused<R, MODE, OPK, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem_fused<R, MODE, OPK, RB>());
 }
 template <class R, int MODE, int OPK>
 void fwd_attrs_opk() {

@@ -372,8 +372,8 @@ long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* p
   };
   const TileMap& m = p.frame;
   const int rnpx = p.ss ? Shapes<1>::Rect::NPX : Shapes<0>::Rect::NPX;
-  const int wnpx = p.ss ? Shapes<1>::Wide::NPX : Shapes<0>::Wide::NPX;
-  const int tnpx = Shapes<0>::Tall::NPX;
+  const int wnpx = p.ss == 2 ? Shapes<2>::Wide::NPX : (p.ss ? Shapes<1>::Wide::NPX : Shapes<0>::Wide::NPX);
+  const int tnpx = p.ss == 2 ? Shapes<2>::Tall::NPX : Shapes<0>::Tall::NPX;
   if (!p.split) {
     for (int bz = 0; bz < p.nzb; ++bz)
       for (int by = 0; by < p.GH; ++by)
@@ -383,17 +383,20 @@ long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* p
           cta(rnpx, m.rw / rnpx, m.rh, x0, y0, nx - 1, ny - 1, form, p.zb, bz, t + (long long)p.GW * (by + p.GH * bz));
         }
   } else {
+    // split: rectangle blocks numbered first, then the frame's; fused (one
+    // launch): per z-block, the rectangle tiles and then the frame tiles
     const int px0 = p.frame.px0, py0 = p.frame.py0;
+    const long long nrect = (long long)p.RW * p.RH, per_z = nrect + p.frame.count;
     for (int bz = 0; bz < p.nzb; ++bz)
       for (int by = 0; by < p.RH; ++by)
         for (int t = 0; t < p.RW; ++t)
           cta(rnpx, m.rw / rnpx, m.rh, px0 + t * m.rw, py0 + by * m.rh, p.frame.px1, p.frame.py1, 0, p.zb, bz,
-              t + (long long)p.RW * (by + p.RH * bz));
+              p.fused ? t + (long long)p.RW * by + per_z * bz : t + (long long)p.RW * (by + p.RH * bz));
     const long long off = (long long)p.RW * p.RH * p.nzb;
     for (int bz = 0; bz < p.nzbf; ++bz)
       for (int t = 0; t < p.frame.count; ++t) {
         const FrameTile f = decode_frame(p.frame, t);
-        const long long bid = off + t + (long long)p.frame.count * bz;
+        const long long bid = p.fused ? nrect + t + per_z * bz : off + t + (long long)p.frame.count * bz;
         if (f.wide)
           cta(wnpx, m.ww / wnpx, m.wh, f.x0, f.y0, f.rx1, f.ry1, 3, p.zbf, bz, bid);
         else
