@@ -24,7 +24,7 @@ inline int choose_zblock(int nx, int ny, int nz, int nrhs) {
   const long long want = 152LL * 2 * 4;
   const long long nzb = (want + tiles - 1) / tiles;
   int zb = (int)((nz + nzb - 1) / nzb);
-  zb = std::max(zb, kMinZblock);
+  zb = std::max(zb, 4);
   zb = std::min(zb, kMaxZb);
   return zb;
 }

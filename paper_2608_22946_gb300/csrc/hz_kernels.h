@@ -57,7 +57,7 @@ void launch_fwd(const StencilCall<R>& c, int opk, cudaStream_t s);
 template <class R, int MODE>
 void fwd_init_attrs();
 // Smallest z-block (planes per CTA) of a stencil launch.
-constexpr int kMinZblock = 4;
+constexpr int kMinZblock = 2;
 long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
                                  int zblock = 0, int zblock_f = 0);
 // Blocks per right-hand side of an adjoint stencil launch (zblock > 0 forces it).

@@ -885,7 +885,7 @@ void autotune_zblocks(hz_handle* H) {
   cudaEvent_t e0, e1;
   HZ_CK(cudaEventCreate(&e0));
   HZ_CK(cudaEventCreate(&e1));
-  const int cand[] = {kMinZblock, 6, 8, 10, 12, 16, 22, 28, 34, 46, 64};
+  const int cand[] = {kMinZblock, 3, 4, 6, 8, 10, 12, 16, 22, 28, 34, 46, 64};
   for (int L = 0; L < 3; ++L) {
     Level& lv = H->lev[L];
     const long long n = lv.N * nr;

@@ -251,7 +251,7 @@ static int adj_zblock(int nx, int ny, int nz, int nrhs) {
   const long long want = 152LL * 2 * 4;
   const long long nzb = (want + tiles - 1) / tiles;
   int zb = (int)((nz + nzb - 1) / nzb);
-  return std::min(std::max(zb, kMinZblock), kMaxZb);
+  return std::min(std::max(zb, 4), kMaxZb);
 }
 
 template <class R, int MODE, int OP>

@@ -171,17 +171,17 @@ def test_package_does_not_use_the_oracle():
 
 def test_reduction_slots_are_sized_by_the_smallest_zblock(lib):
     """The fused-norm partial-sum array is sized from the block count at the
-    smallest z-block (4 planes for both launches); no z-block the heuristic or
-    the autotuner can choose (4 .. 64, frame and rectangle independently)
+    smallest z-block (2 planes for both launches); no z-block the heuristic or
+    the autotuner can choose (2 .. 64, frame and rectangle independently)
     yields more blocks."""
     import paper_2608_22946_gb300 as hz
     for shape, p in [((288, 288, 288), 16), ((224, 224, 224), 16), ((152, 152, 152), 12), ((104, 104, 104), 16),
                      ((300, 116, 40), 8), ((48, 48, 48), 8)]:
         for lev in (0, 1, 2):
             for nrhs in (1, 16):
-                _, worst, _ = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=4, zblock_f=4)
-                for zb in (0, 5, 6, 8, 12, 22, 46, 64):
-                    for zbf in (0, 4, 8, 22, 64):
+                _, worst, _ = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=2, zblock_f=2)
+                for zb in (0, 3, 4, 6, 8, 12, 22, 46, 64):
+                    for zbf in (0, 2, 4, 8, 22, 64):
                         _, b, bad = hz.layout_check(shape, p, level=lev, nrhs=nrhs, zblock=zb, zblock_f=zbf)
                         assert bad == 0 and b <= worst, (shape, lev, nrhs, zb, zbf, b, worst)
 
@@ -200,7 +200,7 @@ def test_adjoint_launch_layout_and_partial_sums(lib):
     assert adj > fwd, (adj, fwd)
     for shape, p in [((288, 288, 288), 16), ((916, 564, 76), 12), ((40, 200, 24), 4), ((48, 48, 48), 8)]:
         for lev in (0, 1, 2):
-            _, worst_f, _ = hz.layout_check(shape, p, level=lev, nrhs=1, zblock=4, zblock_f=4)
+            _, worst_f, _ = hz.layout_check(shape, p, level=lev, nrhs=1, zblock=2, zblock_f=2)
             _, worst_a, _ = hz.layout_check(shape, p, level=lev, op=hz.HZ_OP_A_ADJ, nrhs=1, zblock=4)
             for nrhs in (1, 3, 16):
                 _, a, _ = hz.layout_check(shape, p, level=lev, op=hz.HZ_OP_B_ADJ, nrhs=nrhs)
