@@ -116,12 +116,15 @@ struct FLayout {
   static constexpr size_t dring = MODE == M_J2 ? (size_t)NSTG * TS::PLN * CXB : 0;
   static constexpr size_t y1 = MODE == M_J2 ? (size_t)RB * TS::PLN * CXB : 0;
   static constexpr size_t kap = (size_t)NSTG * TS::NT * TS::NPX * sizeof(R);
+  static constexpr int tabn = (OPK == OPK_Q ? kCtQ : kCtCA + (OPK == OPK_B ? kCtK : 0) + kCtT) * (kMaxSeg + 1);
+  static constexpr size_t tab = (size_t)tabn * sizeof(R);
   static constexpr size_t ez = OPK == OPK_Q ? 0 : (size_t)(kMaxZb + 2) * 2 * CXB;
   static constexpr size_t o_ring = 0;
   static constexpr size_t o_dring = a16(o_ring + ring);
   static constexpr size_t o_y1 = a16(o_dring + dring);
   static constexpr size_t o_kap = a16(o_y1 + y1);
-  static constexpr size_t o_ez = a16(o_kap + kap);
+  static constexpr size_t o_tab = a16(o_kap + kap);
+  static constexpr size_t o_ez = a16(o_tab + tab);
   static constexpr size_t o_red = a16(o_ez + ez);
   static constexpr size_t bytes = o_red + 32 * sizeof(double);
 };
@@ -238,47 +241,15 @@ __device__ __forceinline__ void lds_vec(const double* p, double* d) {
   }
 }
 
-// N values through the read-only data cache (16-byte aligned; float: 8-byte when N = 2)
-template <int N>
-__device__ __forceinline__ void ldg_vec(const float* p, float* d) {
-  if constexpr (N % 4 == 0) {
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
-      d[4 * i] = v.x;
-      d[4 * i + 1] = v.y;
-      d[4 * i + 2] = v.z;
-      d[4 * i + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
-      d[2 * i] = v.x;
-      d[2 * i + 1] = v.y;
-    }
-  }
-}
-template <int N>
-__device__ __forceinline__ void ldg_vec(const double* p, double* d) {
-#pragma unroll
-  for (int i = 0; i < N / 2; ++i) {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
-    d[2 * i] = v.x;
-    d[2 * i + 1] = v.y;
-  }
-}
-
 // NF polynomials of degree DEG stored power-major (c[j * NF + m]), evaluated
-// together at u: one vector load per power (the level's table is a few KB,
-// read by every block through the read-only cache)
+// together at u: one vector load per power
 template <class R, int NF, int DEG>
-__device__ __forceinline__ void horner_pm(const R* __restrict__ c, R u, R* v) {
-  ldg_vec<NF>(c + DEG * NF, v);
+__device__ __forceinline__ void horner_pm(const R* c, R u, R* v) {
+  lds_vec<NF>(c + DEG * NF, v);
 #pragma unroll
   for (int j = DEG - 1; j >= 0; --j) {
     R cj[NF];
-    ldg_vec<NF>(c + j * NF, cj);
+    lds_vec<NF>(c + j * NF, cj);
 #pragma unroll
     for (int m = 0; m < NF; ++m) v[m] = v[m] * u + cj[m];
   }
@@ -326,7 +297,7 @@ __device__ __forceinline__ int seg_of(R kap, int ns, R ds, R inv_ds, R& u) {
 }
 
 // PML transverse weights (alpha_4, alpha_5 / 4, (1 - alpha_4 - alpha_5) / 4) of a
-// row; tT points at the alpha_4 / alpha_5 block of the level's table
+// row; tT points at the alpha_4 / alpha_5 block of the shared-memory table
 template <class R>
 __device__ __forceinline__ RowT<R> eval_t(const R* tT, int seg, R u) {
   R a[2];
@@ -338,7 +309,7 @@ __device__ __forceinline__ RowT<R> eval_t(const R* tT, int seg, R u) {
 template <class R, int OPK>
 __device__ __forceinline__ void eval_c(const R* sT, int ns, int seg, R u, cx<R> shift, RowC<R, OPK == OPK_B>& C) {
   if constexpr (OPK == OPK_Q) {
-    horner_pm<R, 4, 3>(sT + ct_off_Q(ns) + seg * kCtQ, u, C.c);
+    horner_pm<R, 4, 3>(sT + seg * kCtQ, u, C.c);
   } else if constexpr (OPK == OPK_B) {
     R cr[4], km[4];
     horner_pm<R, 4, 5>(sT + seg * kCtCA, u, cr);
@@ -349,6 +320,10 @@ __device__ __forceinline__ void eval_c(const R* sT, int ns, int seg, R u, cx<R> 
     horner_pm<R, 4, 5>(sT + seg * kCtCA, u, C.c);
   }
 }
+
+// the alpha_4 / alpha_5 block of the shared-memory table: [C][K (B only)][T]
+template <int OPK>
+__device__ __forceinline__ int t_block(int ns) { return OPK == OPK_B ? ct_off_T(ns) : ct_off_K(ns); }
 
 // Contribution of one plane to a row at plane offset RHO (= plane - row):
 // shell weights, PML corrections in x / y (Ac, Bc) and, in a z-PML row, the z
@@ -410,7 +385,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   cx<R>* sD = reinterpret_cast<cx<R>*>(smem + LY::o_dring);
   cx<R>* sY1 = reinterpret_cast<cx<R>*>(smem + LY::o_y1);
   R* sK = reinterpret_cast<R*>(smem + LY::o_kap);
-  const R* sT = Lv.ctab;  // the level's coefficient polynomials (global, read-only)
+  R* sT = reinterpret_cast<R*>(smem + LY::o_tab);
   cx<R>* sEz = reinterpret_cast<cx<R>*>(smem + LY::o_ez);
   double* sRed = reinterpret_cast<double*>(smem + LY::o_red);
 
@@ -425,13 +400,23 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   const R ds = a.tab.ds, inv_ds = a.tab.inv_ds;
   const int zlo = Lv.plain_lo[2], zhi = Lv.plain_hi[2];
 
-  // the z-PML factors of rows zb0-1 .. zb1
-  if constexpr (ZP) {
-    for (int t = tid; t < nplanes; t += NT) {
-      const int r = zb0 - 1 + t;
-      const bool ok = r >= 0 && r < nz;
-      sEz[2 * t] = ok ? Lv.eps[2][0][r] : mkc<R>(0, 0);
-      sEz[2 * t + 1] = ok ? Lv.eps[2][1][r] : mkc<R>(0, 0);
+  // coefficient tables (this level) and the z-PML factors of rows zb0-1 .. zb1
+  {
+    const R* g = Lv.ctab;
+    if constexpr (OPK == OPK_Q) {
+      for (int i = tid; i < kCtQ * ns; i += NT) sT[i] = g[ct_off_Q(ns) + i];
+    } else {
+      const int nca = (kCtCA + (CPLX ? kCtK : 0)) * ns;
+      for (int i = tid; i < nca; i += NT) sT[i] = g[i];
+      if constexpr (CORR || ZP)
+        for (int i = tid; i < kCtT * ns; i += NT) sT[nca + i] = g[ct_off_T(ns) + i];
+      if constexpr (ZP)
+        for (int t = tid; t < nplanes; t += NT) {
+          const int r = zb0 - 1 + t;
+          const bool ok = r >= 0 && r < nz;
+          sEz[2 * t] = ok ? Lv.eps[2][0][r] : mkc<R>(0, 0);
+          sEz[2 * t + 1] = ok ? Lv.eps[2][1][r] : mkc<R>(0, 0);
+        }
     }
   }
 
@@ -530,7 +515,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   for (int sl = 0; sl < (HOLD_T ? 3 : 1); ++sl)
 #pragma unroll
     for (int i = 0; i < NPX; ++i) Th[sl][i] = RowT<R>{0, 0, 0};
-  const R* tT = sT + ct_off_T(ns);
+  const R* tT = sT + t_block<OPK>(ns);
   const R om = a.omega_j;
   const int lc0 = (ty + 1) * PWS + NPX * tx + 1;  // halo index of this thread's first column
   int st = 0, stp = NSTG - 1, sti = PREF;       // ring stages of planes k, k-1 and k+PREF
@@ -839,16 +824,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2) k_fwd_fused(Stenc
   const int nrect = tm.ntx * tm.nrow;
   const unsigned bid = (unsigned)(t + (nrect + tm.count) * blockIdx.z);
   const unsigned nb = (unsigned)tm.nblk_total;
-  // small grids: every body carries the z-PML code (fewer bodies, fewer
-  // instruction-cache misses; its flags are uniform and cheap where false)
+  const bool zp = block_in_zpml(a.lv, zblock);
   if (t < nrect) {
     const int x0 = tm.px0 + (t % tm.ntx) * SRect::TWN, y0 = tm.py0 + (t / tm.ntx) * SRect::TYT;
-    fwd_tile<R, MODE, OPK, 0, true, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);
+    if (zp) fwd_tile<R, MODE, OPK, 0, true, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 0, false, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);
     return;
   }
   const FrameTile f = decode_frame(tm, t - nrect);
   if (f.wide) {
-    fwd_tile<R, MODE, OPK, 3, true, SWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+    if (zp) fwd_tile<R, MODE, OPK, 3, true, SWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
+    else fwd_tile<R, MODE, OPK, 3, false, SWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
   } else {
     fwd_tile<R, MODE, OPK, 2, true, STall, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
   }
