@@ -124,6 +124,7 @@ __device__ __forceinline__ R eta_star(R kappa) {
 // ----------------------------------------------------------------------------
 template <class R>
 struct LevelView {
+  int level;                      // 0 = h, 1 = 2h, 2 = 4h
   int nx, ny, nz;                 // nodes per axis (intervals + 1)
   long long N;                    // nodes
   const R* kappa;                 // k(x_i) * ell per node

@@ -104,7 +104,7 @@ constexpr long long kFusedNodes = 1LL << 20;
 // planes are in flight, and the stage of the previous plane stays readable
 template <class R, int MODE, int RB>
 struct FStages {
-  static constexpr int v = (sizeof(R) == 8 || RB > 1) ? 3 : 6;
+  static constexpr int v = (sizeof(R) == 8 || MODE == M_J2 || RB > 1) ? 3 : 6;
 };
 
 template <class R, int MODE, int OPK, class TS, int RB>

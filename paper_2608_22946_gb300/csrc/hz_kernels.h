@@ -58,16 +58,27 @@ template <class R, int MODE>
 void fwd_init_attrs();
 // Smallest z-block (planes per CTA) of a stencil launch.
 constexpr int kMinZblock = 2;
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
-                                 int zblock = 0, int zblock_f = 0);
+// (level 0 runs the accumulation-form kernels of hz_fwd.cuh, levels 1 and 2 the
+// gather-form kernels of hz_fwd_gather.cu; each has its own launch layout)
+long long stencil_blocks_per_rhs(int level, int nx, int ny, int nz, const int* plain_lo, const int* plain_hi,
+                                 int nrhs, int zblock = 0, int zblock_f = 0);
 // Blocks per right-hand side of an adjoint stencil launch (zblock > 0 forces it).
 long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
 // Host replay of a forward stencil application's launch layout on a grid of
 // nx x ny x nz nodes: per-node write counts of right-hand side 0 (or null) and
 // the number of layout violations (defined beside the tiling).
 long long replay_adj_layout(int nx, int ny, int nz, int nrhs, int zblock, unsigned char* counts, long long* blocks);
-long long replay_fwd_layout(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int op, int nrhs,
-                            int zblock, int zblock_f, unsigned char* counts, long long* blocks);
+long long replay_fwd_layout(int level, int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int op,
+                            int nrhs, int zblock, int zblock_f, unsigned char* counts, long long* blocks);
+namespace gather {
+// forward stencil of the coarse levels (hz_fwd_gather.cu)
+template <class R>
+void launch_fwd_gather(const StencilCall<R>& c, int mode, int op, cudaStream_t s);
+long long gather_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
+                                int zblock, int zblock_f);
+long long replay_gather_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs, int zblock,
+                               int zblock_f, unsigned char* counts, long long* blocks);
+}  // namespace gather
 
 // Grid transfers (Eq. full-weighting, Eq. linear-prolongation).
 template <class R>

@@ -349,6 +349,7 @@ template <class R>
 LevelView<R> view(hz_handle* H, int L) {
   const Level& lv = H->lev[L];
   LevelView<R> v;
+  v.level = L;
   v.nx = lv.nx;
   v.ny = lv.ny;
   v.nz = lv.nz;
@@ -757,9 +758,10 @@ void level_dims(const hz_grid& g, int L, Level& lv) {
 
 // Block partial sums of one fused stencil reduction (forward or adjoint
 // launch) on level lv with nrhs right-hand sides, at the z-blocks it will run.
-long long resid_blocks(const Level& lv, int nrhs, bool adjoint) {
+long long resid_blocks(const Level& lv, int level, int nrhs, bool adjoint) {
   return adjoint ? adj_blocks_per_rhs(lv.nx, lv.ny, lv.nz, nrhs)
-                 : stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nrhs, lv.zblock, lv.zblock_f);
+                 : stencil_blocks_per_rhs(level, lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nrhs, lv.zblock,
+                                          lv.zblock_f);
 }
 
 // Per-block partial sums: the vector reductions use at most 1216 x 56, a fused
@@ -768,8 +770,8 @@ long long resid_blocks(const Level& lv, int nrhs, bool adjoint) {
 size_t red_partial_size(const Level* lev, int nrhs) {
   size_t m = 1216 * 56;
   for (int L = 0; L < 3; ++L) {
-    const long long f = stencil_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, lev[L].plain_lo, lev[L].plain_hi, 1,
-                                               kMinZblock, kMinZblock);
+    const long long f = stencil_blocks_per_rhs(L, lev[L].nx, lev[L].ny, lev[L].nz, lev[L].plain_lo, lev[L].plain_hi,
+                                               1, kMinZblock, kMinZblock);
     const long long a = adj_blocks_per_rhs(lev[L].nx, lev[L].ny, lev[L].nz, 1, kMinZblock);
     m = std::max(m, (size_t)std::max(f, a));
   }
@@ -918,9 +920,9 @@ void autotune_zblocks(hz_handle* H) {
       }
       return ms;
     };
-    const bool split = stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock, 64) !=
-                       stencil_blocks_per_rhs(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock,
-                                              kMinZblock);
+    const bool split =
+        stencil_blocks_per_rhs(L, lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock, 64) !=
+        stencil_blocks_per_rhs(L, lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, nr, kMinZblock, kMinZblock);
     for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
       float best_t = 1e30f;
       int best = 0;
@@ -1272,8 +1274,8 @@ hz_status hz_layout_check(const hz_grid* grid, int level, int op, int nrhs, int 
     if (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ)
       *violations = replay_adj_layout(lv.nx, lv.ny, lv.nz, nrhs, zblock, counts_host, blocks);
     else
-      *violations = replay_fwd_layout(lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi, op == HZ_OP_Q ? OP_Q : OP_AB,
-                                      nrhs, zblock, zblock_f, counts_host, blocks);
+      *violations = replay_fwd_layout(level, lv.nx, lv.ny, lv.nz, lv.plain_lo, lv.plain_hi,
+                                      op == HZ_OP_Q ? OP_Q : OP_AB, nrhs, zblock, zblock_f, counts_host, blocks);
   });
   g_create_error = tmp.err;
   return st;
@@ -1726,7 +1728,7 @@ extern "C" hz_status iofd_residual_static(hz_handle* H, int level, int op, int p
     const Level& lv = H->lev[level];
     const bool adj0 = (op == HZ_OP_A_ADJ || op == HZ_OP_B_ADJ);
     // partial sums of the launch that will run (forward and adjoint tile differently)
-    const long long need = resid_blocks(lv, nrhs, adj0) * nrhs;
+    const long long need = resid_blocks(lv, level, nrhs, adj0) * nrhs;
     HZ_REQUIRE(need <= kResidStaticPartials,
                "grid too large for the static scratch (" + std::to_string(need) + " block partial sums > " +
                    std::to_string(kResidStaticPartials) + ")");

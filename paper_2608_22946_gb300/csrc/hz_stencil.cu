@@ -283,6 +283,10 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
     k_j1<R><<<blocks, 256, 0, s>>>(c, adjoint ? 1 : 0);
     return;
   }
+  if (!adjoint && c.lv.level > 0) {
+    gather::launch_fwd_gather<R>(c, mode, op, s);
+    return;
+  }
   if (!adjoint) {
     const int opk = fwd_opk(c, op);
     if (op == OP_Q) {
@@ -311,8 +315,9 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
 
 // Blocks per right-hand side of a forward stencil launch on this grid (the
 // size of the per-block partial-sum array its fused reductions need).
-long long stencil_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int nrhs,
-                                 int zblock, int zblock_f) {
+long long stencil_blocks_per_rhs(int level, int nx, int ny, int nz, const int* plain_lo, const int* plain_hi,
+                                 int nrhs, int zblock, int zblock_f) {
+  if (level > 0) return gather::gather_blocks_per_rhs(nx, ny, nz, plain_lo, plain_hi, nrhs, zblock, zblock_f);
   const int zb = zblock > 0 ? zblock : choose_zblock(nx, ny, nz, nrhs);
   const FwdPlan p = plan_layout(nx, ny, nz, plain_lo, plain_hi, true, zb, zblock_f);
   return p.blocks();
@@ -334,8 +339,9 @@ long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock) {
 // x), a block id out of range or repeated.  (The kernels use forms 0, 2, 3.)  counts (nx * ny * nz bytes, or
 // null) receives how often each node of right-hand side 0 is written,
 // saturating at 255.
-long long replay_fwd_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs, int zblock,
-                            int zblock_f, unsigned char* counts, long long* blocks) {
+long long replay_fwd_layout(int level, int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs,
+                            int zblock, int zblock_f, unsigned char* counts, long long* blocks) {
+  if (level > 0) return gather::replay_gather_layout(nx, ny, nz, plo, phi, op, nrhs, zblock, zblock_f, counts, blocks);
   const bool ab = op == OP_AB;
   const int zb = zblock > 0 ? zblock : choose_zblock(nx, ny, nz, nrhs);
   const FwdPlan p = plan_layout(nx, ny, nz, plo, phi, ab, zb, zblock_f);
