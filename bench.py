@@ -315,7 +315,7 @@ def run_gpu(args):
     sources, scaling = rank_sources(all_sources, how, world, rank)
     if how == "batch":
         nrhs = len(sources)
-    params = hz.default_params(tol=1e-6, precision=hz.HZ_C64)
+    params = hz.default_params(tol=1e-6, precision=hz.HZ_C64, block=1 if args.block else 0)
     noconv = False
     if args.max_pc:
         # profiling runs: cap the preconditioner calls (same kernel mix, bounded length)
@@ -376,6 +376,8 @@ def run_gpu(args):
                          "grid_intervals": w.n, "n_pml": w.n_pml, "fine_nodes": N, "sources": int(n_src_all),
                          "rhs_in_flight": nrhs, "ppw": 6, "tol": 1e-6,
                          "precision": "c64 hierarchy, FP64 outer scalars + refinement",
+                         "krylov": "block FGMRES over the right-hand sides in flight" if args.block
+                                   else "independent FGMRES per right-hand side (batched kernels)",
                          "parallelism": (f"replicas x{world}, sources split across ranks" if scaling == "strong"
                                          else f"replicas x{world}"),
                          "l2": l2_note(N, nrhs)},
@@ -422,6 +424,12 @@ def run_gpu(args):
         # --- end to end through the public API with host buffers
         u_host = torch.empty((nrhs,) + s.shape, dtype=torch.complex128).pin_memory()
         u2 = torch.empty_like(v)
+        # a second handle beside the resident one must fit (the 961^3 workload
+        # holds 213 GiB): otherwise release the resident handle first
+        free_b, _ = torch.cuda.mem_get_info()
+        if hz.workspace_bytes(w.n, w.n_pml, w.h, w.omega, params=params, max_nrhs=nrhs) > 0.9 * free_b:
+            s.close()
+            torch.cuda.empty_cache()
         e2e_t = []
         src_bytes = len(sources) * (3 * 4 + 2 * 8)
         for it in range(1 + args.e2e_steps if args.e2e_steps > 0 else 0):
@@ -516,30 +524,35 @@ def fp64_leg(hz, w, sources, v_mixed, t_mixed, params):
 
 
 def run_stencil_only(args):
-    """Time the fine-grid complex64 A_h apply alone (the kernel the roofline
-    line reports), K launches after 3 warm-ups, inputs larger than L2."""
+    """Time one complex64 operator application alone (default: the fine-grid
+    A_h apply the roofline line reports; --level / --op select another level
+    and operator), K launches after 3 warm-ups.  --no-autotune keeps the fixed
+    z-block heuristic (fewer launches before the timed ones, for profilers)."""
     import torch
     import paper_2608_22946_gb300 as hz
     w, _, _, _, _ = resolve_workload(args.workload)
-    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=1)
-    x = torch.randn((1,) + s.shape, dtype=torch.complex64, device="cuda")
+    params = hz.default_params(autotune=0 if args.no_autotune else 1)
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=1)
+    L, op = args.level, getattr(hz, "HZ_OP_" + args.op)
+    x = torch.randn((1,) + s.level_shape[L], dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     for _ in range(3):
-        s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+        s.iofd_apply(x, op=op, level=L, out=y, stream=stream)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        s.iofd_apply(x, op=hz.HZ_OP_A, level=0, out=y, stream=stream)
+        s.iofd_apply(x, op=op, level=L, out=y, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1000.0 / args.steps
     pk, _ = peaks()
-    gbs = 20 * w.N / t / 1e9
-    print(json.dumps({"kernel": "k_fwd A_h complex64", "workload": w.name, "n": w.n, "nodes": w.N,
-                      "ms": 1000 * t, "gupdates_per_s": w.N / t / 1e9, "gb_per_s": gbs,
+    NL = x[0].numel()
+    gbs = 20 * NL / t / 1e9
+    print(json.dumps({"kernel": f"forward stencil {args.op} complex64, level {L}", "workload": w.name, "n": w.n,
+                      "nodes": NL, "ms": 1000 * t, "gupdates_per_s": NL / t / 1e9, "gb_per_s": gbs,
                       "frac_hbm": gbs / pk["hbm_gbs"]}), flush=True)
     s.close()
 
@@ -611,7 +624,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--block", action="store_true",
+                    help="block FGMRES over the right-hand sides in flight (multi-source workloads)")
     ap.add_argument("--stencil-only", action="store_true")
+    ap.add_argument("--level", type=int, default=0, help="--stencil-only: grid level (0 = h, 1 = 2h, 2 = 4h)")
+    ap.add_argument("--op", default="A", choices=["A", "B", "Q"], help="--stencil-only: operator")
+    ap.add_argument("--no-autotune", action="store_true", help="--stencil-only: fixed z-block heuristic")
     ap.add_argument("--max-pc", type=int, default=0, help="profiling only: cap preconditioner calls")
     ap.add_argument("--paper-media", action="store_true",
                     help="the paper's benchmark media (homogeneous, lens, wedge, barrier) at tol 1e-4")

@@ -101,6 +101,16 @@ typedef struct {
                           (default).  0: the paper's protocol (Sec. 5.2, Table 4): one
                           complex64 FGMRES(m_out) solve stopped by its own complex64 true
                           residual at tol, no refinement pass; rel_res is that residual */
+  int block;           /* 0: an independent FGMRES(m_out) per right-hand side in flight
+                          (batched operator and preconditioner applications; default).
+                          1: block flexible GMRES (the block Krylov method for multiple
+                          right-hand sides of Sec. 7): the right-hand sides in flight, in
+                          groups of at most 16, share one basis; each block step applies
+                          the preconditioner to the group's basis block and counts as one
+                          preconditioner call; each right-hand side takes the minimal
+                          residual over the whole block space.  A numerically
+                          rank-deficient initial block (a zero or repeated right-hand
+                          side) falls back to the independent method for that solve. */
 } hz_params;
 
 typedef struct {
@@ -120,7 +130,8 @@ typedef struct hz_handle hz_handle;
 
 /* Table 4 defaults (Sec. 6.1): m_out 5, m_h 2 / nJ_h 2 / w_h 0.8, c_2h 2,
  * m_2h 10, nJ_2h 2 / w_2h 0.8, m_4h 4 / nJ_4h 2 / w_4h 0.2, sigma 0.9,
- * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8, autotune 1, refine 1. */
+ * tol 1e-4, precision HZ_C64, inner_tol 1e-5, max_pc 1000, max_refine 8, autotune 1, refine 1,
+ * block 0. */
 void hz_default_params(hz_params* p);
 
 /* Create a solver for one frequency and velocity model.

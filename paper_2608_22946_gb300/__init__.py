@@ -44,7 +44,8 @@ class HzParams(ctypes.Structure):
                 ("nJ_2h", ctypes.c_int), ("m_4h", ctypes.c_int), ("nJ_4h", ctypes.c_int),
                 ("w_h", ctypes.c_double), ("w_2h", ctypes.c_double), ("w_4h", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("autotune", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("autotune", ctypes.c_int), ("refine", ctypes.c_int),
+                ("block", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):

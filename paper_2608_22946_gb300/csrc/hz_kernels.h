@@ -70,6 +70,27 @@ long long adj_blocks_per_rhs(int nx, int ny, int nz, int nrhs, int zblock = 0);
 long long replay_adj_layout(int nx, int ny, int nz, int nrhs, int zblock, unsigned char* counts, long long* blocks);
 long long replay_fwd_layout(int level, int nx, int ny, int nz, const int* plain_lo, const int* plain_hi, int op,
                             int nrhs, int zblock, int zblock_f, unsigned char* counts, long long* blocks);
+// Columns of a block Krylov basis: column t at base + (t / s) * bstride + (t % s) * n
+// elements (blocks of s consecutive columns of n nodes, blocks bstride apart).
+struct BlockCols {
+  const void* base;
+  long long bstride;
+  long long n;
+  int s;
+  int count;
+};
+constexpr int kBlockMaxS = 16;   // right-hand sides sharing one block FGMRES basis
+constexpr int kBlockMaxP = 256;  // basis columns entering one block update (m_out * s)
+// doubles of the Gram kernel's per-chunk partial sums for p x q blocks of n nodes
+size_t block_gram_partial_doubles(long long n, int p, int q);
+// out (p x q complex double, row-major) = X^H Y; partial: block_gram_partial_doubles
+template <class R>
+void launch_block_gram(const BlockCols& X, const BlockCols& Y, double* partial, double* out, cudaStream_t s);
+// Y_c = beta Y_c + sum_t X_t C[t][c] for the q <= 16 columns of Y (stride X.n);
+// C complex double p x q row-major on the device; Y may be X itself
+template <class R>
+void launch_block_update(const BlockCols& X, cx<R>* Y, int q, const double* C, double beta, cudaStream_t s);
+void block_init_attrs();
 namespace gather {
 // forward stencil of the coarse levels (hz_fwd_gather.cu)
 template <class R>

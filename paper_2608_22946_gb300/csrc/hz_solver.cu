@@ -118,6 +118,8 @@ struct Work {
   double *beta_o = nullptr, *beta_s = nullptr, *beta_k = nullptr, *scale_o = nullptr, *scale_s = nullptr,
          *scale_k = nullptr;
   double *yo = nullptr, *ys = nullptr, *yk = nullptr, *yc = nullptr, *nrm = nullptr;
+  // block FGMRES: Gram partial sums per node chunk, one Gram block, one coefficient block
+  double *bpart = nullptr, *bgram = nullptr, *bcoef = nullptr;
 };
 
 template <class R> struct Sel;
@@ -719,6 +721,12 @@ void plan_work(Alloc& al, Work<R>& W, const Level* lev, const hz_params& p, int 
   W.scale_s = sc(nrhs);
   W.scale_k = sc(nrhs);
   W.nrm = sc(nrhs);
+  if (nrhs >= 2) {
+    const int S = std::min(nrhs, kBlockMaxS);
+    W.bpart = sc(block_gram_partial_doubles(lev[0].N, p.m_out * S, S));
+    W.bgram = sc((size_t)p.m_out * S * S * 2);
+    W.bcoef = sc((size_t)p.m_out * S * S * 2);
+  }
   W.ready = !al.count_only;
 }
 
@@ -731,6 +739,7 @@ void check_params(const hz_params& p) {
   HZ_REQUIRE(p.nJ_h >= 1 && p.nJ_2h >= 1 && p.nJ_4h >= 1, "Jacobi sweep counts must be >= 1");
   HZ_REQUIRE(p.tol > 0 && p.max_pc >= 1, "tol must be > 0 and max_pc >= 1");
   HZ_REQUIRE(p.precision == HZ_C64 || p.precision == HZ_C128, "precision must be HZ_C64 or HZ_C128");
+  HZ_REQUIRE(p.block == 0 || p.block == 1, "block must be 0 or 1");
 }
 
 void check_grid(const hz_grid& g) {
@@ -1059,6 +1068,247 @@ double outer_fgmres(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, 
   return relmax;
 }
 
+// ----------------------------------------------------------------------------
+// block flexible GMRES(m_out) over groups of right-hand sides (Sec. 7's block
+// Krylov method for multiple right-hand sides)
+// ----------------------------------------------------------------------------
+// One basis per group of S <= 16 right-hand sides: the block residual
+// R_0 = V_0 R_hat, then per step Z_j = M(V_j) (the three-grid preconditioner
+// on the S columns), W = A Z_j, block classical Gram-Schmidt against
+// V_0 .. V_j in two passes, W = V_{j+1} H_{j+1,j}.  Thin QR factors come from
+// Cholesky-QR applied twice (Gram block on the device, Cholesky of the S x S
+// block in FP64 on the host).  The block Hessenberg matrix is banded (S
+// sub-diagonals, the last block upper triangular) and is reduced by Givens
+// rotations in FP64 on the host; the rotated right-hand side block gives each
+// column's residual estimate.  Column t of block j of the basis is
+// Vo + j * vs + (r0 + t) * N, so the group's blocks are the same workspace
+// the independent solves use.
+using Cd = std::complex<double>;
+
+// G = R^H R for an S x S Hermitian block (row-major); R upper triangular.
+// False when a pivot falls below rel times the largest diagonal entry.
+bool chol_upper(const std::vector<Cd>& G, int S, double rel, std::vector<Cd>& Rm) {
+  Rm.assign((size_t)S * S, Cd(0.0));
+  double dmax = 0.0;
+  for (int i = 0; i < S; ++i) dmax = std::max(dmax, G[(size_t)i * S + i].real());
+  if (!(dmax > 0.0) || !std::isfinite(dmax)) return false;
+  for (int i = 0; i < S; ++i) {
+    Cd d = G[(size_t)i * S + i];
+    for (int k = 0; k < i; ++k) d -= std::norm(Rm[(size_t)k * S + i]);
+    if (!(d.real() > rel * dmax)) return false;
+    const double rii = std::sqrt(d.real());
+    Rm[(size_t)i * S + i] = rii;
+    for (int j = i + 1; j < S; ++j) {
+      Cd t = G[(size_t)i * S + j];
+      for (int k = 0; k < i; ++k) t -= std::conj(Rm[(size_t)k * S + i]) * Rm[(size_t)k * S + j];
+      Rm[(size_t)i * S + j] = t / rii;
+    }
+  }
+  return true;
+}
+
+// inverse of an upper-triangular S x S matrix (row-major)
+std::vector<Cd> upper_inverse(const std::vector<Cd>& Rm, int S) {
+  std::vector<Cd> X((size_t)S * S, Cd(0.0));
+  for (int c = 0; c < S; ++c)
+    for (int i = c; i >= 0; --i) {
+      Cd t = (i == c) ? Cd(1.0) : Cd(0.0);
+      for (int k = i + 1; k <= c; ++k) t -= Rm[(size_t)i * S + k] * X[(size_t)k * S + c];
+      X[(size_t)i * S + c] = t / Rm[(size_t)i * S + i];
+    }
+  return X;
+}
+
+template <class R>
+struct BlockGroup {
+  hz_handle* H;
+  Work<R>& W;
+  long long N, vs;
+  int r0, S;
+  BlockCols cols(const cx<R>* base, int count) const { return BlockCols{base + (long long)r0 * N, vs, N, S, count}; }
+  cx<R>* blk(cx<R>* base, int j) const { return base + (long long)j * vs + (long long)r0 * N; }
+  // G = X^H Y, p x q row-major, on the host
+  std::vector<Cd> gram(const BlockCols& X, const BlockCols& Y) const {
+    launch_block_gram<R>(X, Y, W.bpart, W.bgram, H->st);
+    HZ_LAUNCHED();
+    std::vector<double> g = host_copy(W.bgram, 2 * X.count * Y.count, H->st);
+    std::vector<Cd> G((size_t)X.count * Y.count);
+    for (size_t e = 0; e < G.size(); ++e) G[e] = Cd(g[2 * e], g[2 * e + 1]);
+    return G;
+  }
+  // Y = beta Y + X C (C: p x q row-major)
+  void update(const BlockCols& X, cx<R>* Y, const std::vector<Cd>& Cm, double beta) const {
+    HZ_CK(cudaMemcpyAsync(W.bcoef, Cm.data(), Cm.size() * sizeof(Cd), cudaMemcpyHostToDevice, H->st));
+    launch_block_update<R>(X, Y, S, W.bcoef, beta, H->st);
+    HZ_LAUNCHED();
+  }
+  // thin QR of block j of the basis in place by Cholesky-QR twice; R (S x S, upper)
+  bool cholqr2(int j, std::vector<Cd>& Rout) const {
+    // pivots below this fraction mean a condition number beyond what two
+    // Cholesky-QR passes orthogonalise in the working precision
+    const double rel = sizeof(R) == 4 ? 1e-7 : 1e-14;
+    const BlockCols B = cols(W.Vo + (long long)j * vs, S);
+    cx<R>* Bp = blk(W.Vo, j);
+    std::vector<Cd> R1, R2;
+    if (!chol_upper(gram(B, B), S, rel, R1)) return false;
+    update(B, Bp, upper_inverse(R1, S), 0.0);
+    if (!chol_upper(gram(B, B), S, 1e-3, R2)) return false;
+    update(B, Bp, upper_inverse(R2, S), 0.0);
+    Rout.assign((size_t)S * S, Cd(0.0));
+    for (int i = 0; i < S; ++i)
+      for (int c = i; c < S; ++c) {
+        Cd t = 0.0;
+        for (int k = i; k <= c; ++k) t += R2[(size_t)i * S + k] * R1[(size_t)k * S + c];
+        Rout[(size_t)i * S + c] = t;
+      }
+    return true;
+  }
+};
+
+// One group of S right-hand sides starting at r0; returns the largest relative
+// true residual of the group's last restart, or a negative value when the
+// initial block is numerically rank-deficient (nothing has been changed then).
+template <class R>
+double block_fgmres_group(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, int r0, int S, bool adj,
+                          const std::vector<double>& bn, double tol, int max_pc, int& pc, bool inner) {
+  Work<R>& W = Sel<R>::w(H);
+  const int m = H->p.m_out;
+  const long long N = H->lev[0].N, vs = N * nrhs;
+  BlockGroup<R> G{H, W, N, vs, r0, S};
+  const int ldE = (m + 1) * S;
+  double relmax = 0.0, prev_rel = HUGE_VAL;
+  bool est_converged = false, first = true;
+  for (;;) {
+    cx<R>* V0 = G.blk(W.Vo, 0);
+    resid<R>(H, 0, false, adj, b + (long long)r0 * N, x + (long long)r0 * N, V0, S,
+             reducer(H, W.nrm, W.beta_o, W.scale_o));
+    std::vector<double> beta = host_copy(W.beta_o, S, H->st);
+    relmax = 0.0;
+    for (int c = 0; c < S; ++c) {
+      if (!std::isfinite(beta[c])) throw Fail{HZ_ENONFINITE, "non-finite residual norm in the block FGMRES"};
+      relmax = std::max(relmax, bn[r0 + c] > 0 ? beta[c] / bn[r0 + c] : 0.0);
+    }
+    if (relmax <= tol || pc >= max_pc) break;
+    if (inner && relmax > 0.9 * prev_rel) break;
+    prev_rel = relmax;
+    std::vector<Cd> Rh;
+    if (!G.cholqr2(0, Rh)) {
+      if (first) return -1.0;
+      break;  // a later rank-deficient residual block: the caller's true residual decides
+    }
+    first = false;
+    // banded Hessenberg (column-major, ld ldE), rotated right-hand side block E
+    std::vector<Cd> Hh((size_t)ldE * m * S, Cd(0.0)), E((size_t)ldE * S, Cd(0.0));
+    for (int i = 0; i < S; ++i)
+      for (int c = i; c < S; ++c) E[(size_t)c * ldE + i] = Rh[(size_t)i * S + c];
+    struct Rot {
+      int i;
+      double c;
+      Cd s;
+    };
+    std::vector<Rot> rots;
+    auto rotate = [](const Rot& q, Cd* v) {
+      const Cd t1 = v[q.i], t2 = v[q.i + 1];
+      v[q.i] = q.c * t1 + q.s * t2;
+      v[q.i + 1] = q.c * t2 - std::conj(q.s) * t1;
+    };
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      precond<R>(H, G.blk(W.Vo, j), G.blk(W.Zo, j), S, adj);
+      ++pc;
+      cx<R>* Wb = G.blk(W.Vo, j + 1);
+      apply<R>(H, 0, false, adj, G.blk(W.Zo, j), Wb, S);
+      const BlockCols Vset = G.cols(W.Vo, (j + 1) * S), Wset = G.cols(W.Vo + (long long)(j + 1) * vs, S);
+      std::vector<Cd> Hacc((size_t)(j + 1) * S * S, Cd(0.0));
+      for (int pass = 0; pass < 2; ++pass) {
+        std::vector<Cd> Hp = G.gram(Vset, Wset);
+        std::vector<Cd> neg(Hp.size());
+        for (size_t e = 0; e < Hp.size(); ++e) {
+          Hacc[e] += Hp[e];
+          neg[e] = -Hp[e];
+        }
+        G.update(Vset, Wb, neg, 1.0);
+      }
+      std::vector<Cd> Rsub;
+      const bool full = G.cholqr2(j + 1, Rsub);
+      // block column j of the Hessenberg matrix, then the old and new rotations
+      for (int c = 0; c < S; ++c) {
+        const int q = j * S + c;
+        Cd* col = &Hh[(size_t)q * ldE];
+        for (int i = 0; i < (j + 1) * S; ++i) col[i] = Hacc[(size_t)i * S + c];
+        if (full)
+          for (int i = 0; i <= c; ++i) col[(j + 1) * S + i] = Rsub[(size_t)i * S + c];
+        for (const Rot& q2 : rots) rotate(q2, col);
+        for (int r = q + S; r > q; --r) {
+          const Cd a = col[r - 1], bb = col[r];
+          if (bb == Cd(0.0)) continue;
+          const double na = std::abs(a), nb = std::abs(bb), rr = std::hypot(na, nb);
+          Rot g{r - 1, 0.0, Cd(0.0)};
+          if (na == 0.0) {
+            g.c = 0.0;
+            g.s = 1.0;
+          } else {
+            g.c = na / rr;
+            g.s = (a / na) * std::conj(bb) / rr;
+          }
+          rotate(g, col);
+          col[r] = 0.0;
+          for (int e = 0; e < S; ++e) rotate(g, &E[(size_t)e * ldE]);
+          rots.push_back(g);
+        }
+      }
+      k = j + 1;
+      bool all_conv = true;
+      for (int c = 0; c < S; ++c) {
+        double e2 = 0.0;
+        for (int i = k * S; i < (k + 1) * S; ++i) e2 += std::norm(E[(size_t)c * ldE + i]);
+        const double est = bn[r0 + c] > 0 ? std::sqrt(e2) / bn[r0 + c] : 0.0;
+        if (!std::isfinite(est)) throw Fail{HZ_ENONFINITE, "non-finite block Arnoldi residual estimate"};
+        if (est > tol) all_conv = false;
+      }
+      // a rank-deficient block W ends the cycle; its zeroed sub-diagonal block
+      // is no convergence evidence, so the next restart's true residual decides
+      est_converged = all_conv && full;
+      if (all_conv || !full || pc >= max_pc) break;
+    }
+    // Y = R^-1 E[0 : kS] (k S x S), then x += [Z_0 .. Z_{k-1}] Y
+    const int KS = k * S;
+    std::vector<Cd> Y((size_t)KS * S, Cd(0.0));
+    for (int c = 0; c < S; ++c)
+      for (int i = KS - 1; i >= 0; --i) {
+        Cd t = E[(size_t)c * ldE + i];
+        for (int l = i + 1; l < KS; ++l) t -= Hh[(size_t)l * ldE + i] * Y[(size_t)l * S + c];
+        const Cd d = Hh[(size_t)i * ldE + i];
+        Y[(size_t)i * S + c] = std::abs(d) > 0 ? t / d : Cd(0.0);
+      }
+    G.update(G.cols(W.Zo, KS), x + (long long)r0 * N, Y, 1.0);
+    if (inner && (est_converged || pc >= max_pc)) break;
+  }
+  return relmax;
+}
+
+// The outer Krylov solve: block FGMRES over groups of at most kBlockMaxS
+// right-hand sides when selected (independent FGMRES for a group whose initial
+// block is rank-deficient), else the independent batched FGMRES.
+template <class R>
+double outer_solve(hz_handle* H, const cx<R>* b, cx<R>* x, int nrhs, bool adj, const std::vector<double>& bn,
+                   double tol, int max_pc, int& pc, bool inner = false) {
+  if (!H->p.block || nrhs < 2) return outer_fgmres<R>(H, b, x, nrhs, adj, bn, tol, max_pc, pc, inner);
+  const long long N = H->lev[0].N;
+  double relmax = 0.0;
+  for (int r0 = 0; r0 < nrhs; r0 += kBlockMaxS) {
+    const int S = std::min(kBlockMaxS, nrhs - r0);
+    double rel = S >= 2 ? block_fgmres_group<R>(H, b, x, nrhs, r0, S, adj, bn, tol, max_pc, pc, inner) : -1.0;
+    if (rel < 0.0) {
+      // the independent method on this group alone (its own columns, scales and norms)
+      std::vector<double> bg(bn.begin() + r0, bn.begin() + r0 + S);
+      rel = outer_fgmres<R>(H, b + (long long)r0 * N, x + (long long)r0 * N, S, adj, bg, tol, max_pc, pc, inner);
+    }
+    relmax = std::max(relmax, rel);
+  }
+  return relmax;
+}
+
 std::vector<double> norms(hz_handle* H, const cx<double>* v, int nrhs) {
   launch_norm2<double>(v, (int)H->lev[0].N, nrhs, reducer(H, H->s_nrm), H->st);
   HZ_LAUNCHED();
@@ -1081,7 +1331,7 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
   HZ_LAUNCHED();
   if (p.precision == HZ_C128) {
     ensure_work<double>(H);
-    o.rel = outer_fgmres<double>(H, b, x, nrhs, adj, bn, p.tol, p.max_pc, o.pc);
+    o.rel = outer_solve<double>(H, b, x, nrhs, adj, bn, p.tol, p.max_pc, o.pc);
     return o;
   }
   ensure_work<float>(H);
@@ -1098,7 +1348,7 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     launch_c128_to_c64_scaled(b, H->b64, H->s_inv, (int)N, nrhs, H->st);
     launch_zero<float>(H->x64, N * nrhs, H->st);
     HZ_LAUNCHED();
-    o.rel = outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, p.tol, p.max_pc, o.pc);
+    o.rel = outer_solve<float>(H, H->b64, H->x64, nrhs, adj, one, p.tol, p.max_pc, o.pc);
     launch_add_c64_to_c128_scaled(H->x64, x, H->s_root, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
     HZ_CK(cudaStreamSynchronize(H->st));
@@ -1139,7 +1389,7 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
     std::vector<double> one(nrhs);
     for (int r = 0; r < nrhs; ++r) one[r] = rn[r] > 0 ? 1.0 : 0.0;
     double inner = std::max(p.inner_tol, need);
-    outer_fgmres<float>(H, H->b64, H->x64, nrhs, adj, one, inner, p.max_pc, o.pc, true);
+    outer_solve<float>(H, H->b64, H->x64, nrhs, adj, one, inner, p.max_pc, o.pc, true);
     launch_add_c64_to_c128_scaled(H->x64, x, H->s_root, (int)N, nrhs, H->st);
     HZ_LAUNCHED();
     x_zero = false;
@@ -1235,6 +1485,7 @@ void hz_default_params(hz_params* p) {
   p->max_refine = 8;
   p->autotune = 1;
   p->refine = 1;
+  p->block = 0;
 }
 
 const char* hz_last_error(const hz_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -1303,6 +1554,7 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     const char* ng = std::getenv("HZ_NO_GRAPH");
     H->use_graphs = !(ng && ng[0] == '1');
     init_kernel_attributes();
+    block_init_attrs();
     HZ_LAUNCHED();
     auto t0 = std::chrono::steady_clock::now();
     plan_all(H, false);

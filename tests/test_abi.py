@@ -40,7 +40,7 @@ def test_default_params_are_table4(lib):
     p = hz.default_params()
     assert (p.m_out, p.m_h, p.nJ_h, p.c_2h, p.m_2h, p.nJ_2h, p.m_4h, p.nJ_4h) == (5, 2, 2, 2, 10, 2, 4, 2)
     assert (p.w_h, p.w_2h, p.w_4h, p.sigma, p.tol) == (0.8, 0.8, 0.2, 0.9, 1e-4)
-    assert (p.precision, p.refine, p.autotune) == (hz.HZ_C64, 1, 1)
+    assert (p.precision, p.refine, p.autotune, p.block) == (hz.HZ_C64, 1, 1, 0)
 
 
 def test_workspace_bytes_and_validation(lib):
