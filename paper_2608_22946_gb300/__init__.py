@@ -129,6 +129,13 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _nrhs(t, n, name):
+    """Right-hand sides in a field tensor of level size n (a whole number of fields)."""
+    if t.numel() == 0 or t.numel() % n:
+        raise ValueError(f"{name}: {t.numel()} elements is not a whole, non-zero number of fields of {n} nodes")
+    return t.numel() // n
+
+
 def _check_field(t, dtype, n, name):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
@@ -198,9 +205,7 @@ class Solver:
         import torch
         prec = HZ_C64 if x.dtype == torch.complex64 else HZ_C128
         n = self.N[level]
-        if x.numel() % n:
-            raise ValueError(f"x: {x.numel()} elements is not a whole number of level-{level} fields ({n})")
-        nrhs = x.numel() // n
+        nrhs = _nrhs(x, n, "x")
         _check_field(x, x.dtype, n * nrhs, "x")
         y = torch.empty_like(x) if out is None else out
         _check_field(y, x.dtype, n * nrhs, "out")
@@ -218,7 +223,7 @@ class Solver:
         n = self.N[level]
         if g.numel() % n:
             raise ValueError(f"g: {g.numel()} elements is not a whole number of level-{level} fields ({n})")
-        nrhs = g.numel() // n
+        nrhs = _nrhs(g, n, "g")
         _check_field(g, g.dtype, n * nrhs, "g")
         y = torch.empty_like(g) if out is None else out
         _check_field(y, g.dtype, n * nrhs, "out")
@@ -237,9 +242,7 @@ class Solver:
         import torch
         prec = HZ_C64 if x.dtype == torch.complex64 else HZ_C128
         n = self.N[level]
-        if x.numel() % n:
-            raise ValueError(f"x: {x.numel()} elements is not a whole number of level-{level} fields ({n})")
-        nrhs = x.numel() // n
+        nrhs = _nrhs(x, n, "x")
         _check_field(x, x.dtype, n * nrhs, "x")
         _check_field(g, x.dtype, n * nrhs, "g")
         r = torch.empty_like(x) if out is None else out
@@ -258,7 +261,7 @@ class Solver:
         import torch
         prec = HZ_C64 if r.dtype == torch.complex64 else HZ_C128
         n = self.N[0]
-        nrhs = r.numel() // n
+        nrhs = _nrhs(r, n, "r")
         _check_field(r, r.dtype, n * nrhs, "r")
         z = torch.empty_like(r) if out is None else out
         self._ok(self._lib.threegrid_precond(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),

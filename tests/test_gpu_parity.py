@@ -129,6 +129,12 @@ def test_apply_rejects_bad_arguments(pair, hz):
     with pytest.raises(hz.HzError) as e:
         s.iofd_apply(x, op=hz.HZ_OP_Q, level=1)
     assert e.value.status == hz.HZ_EINVAL
+    # a field tensor that is not a whole number of fields is refused by the binding
+    part = torch.zeros(s.N[0] + 1, dtype=torch.complex64, device="cuda")
+    for call in (lambda: s.iofd_apply(part), lambda: s.threegrid_precond(part),
+                 lambda: s.iofd_jacobi(part), lambda: s.residual_static(part, part)):
+        with pytest.raises(ValueError, match="whole"):
+            call()
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
