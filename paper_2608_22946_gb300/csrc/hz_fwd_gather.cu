@@ -17,6 +17,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "hz_gram_solve.cuh"
 #include "hz_kernels.h"
 
 namespace hz {
@@ -229,12 +230,12 @@ __host__ __device__ __forceinline__ FrameTile decode_frame(const TileMap& m, int
 }
 
 // One CTA: the tile of shape TL with origin (x0, y0), writing the columns up to
-// (rx1, ry1) (both inside the grid), over z-block blockIdx.z.
+// (rx1, ry1) (both inside the grid), over z-block bz.
 // Row forms: 0 shell (x and y outside the PML), 1 PML along x only, 2 general,
 // 3 PML along y only.  Forms 1 and 3 drop the first-difference term of the
 // PML-free axis, whose achk is exactly zero.
 template <class R, int MODE, int OP, int FORM, class TL>
-__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, const TileMap& tm, int rhs, int x0,
+__device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, int bz, const TileMap& tm, int rhs, int x0,
                                          int y0, int rx1, int ry1, unsigned bid, cx<R>* sX, cx<R>* sD, cx<R>* sY1,
                                          const R* sTab, double* sRed, R (*sKc)[NT], cx<R> (*sGc)[NT]) {
   constexpr int PWS = TL::PWS, PLN = TL::PLN;
@@ -242,7 +243,7 @@ __device__ __forceinline__ void fwd_body(const StencilCall<R>& a, int zblock, co
   const LevelView<R>& L = a.lv;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int tx = tid % TL::TXS, ty = tid / TL::TXS;
-  const int zb0 = blockIdx.z * zblock;
+  const int zb0 = bz * zblock;
   const int zb1 = min(zb0 + zblock, L.nz);
   const int nplanes = zb1 - zb0 + 2;
   const long long N = L.N;
@@ -492,21 +493,21 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) 
       // strips below / above the rectangle: PML along y only away from the corners
       const bool xplain = f.x0 >= a.lv.plain_lo[0] && f.x0 + TileW::TXS - 1 <= a.lv.plain_hi[0];
       if (xplain)
-        fwd_body<R, MODE, OP, 3, TileW>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+        fwd_body<R, MODE, OP, 3, TileW>(a, zblock, (int)blockIdx.z, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
                                         sKc, sGc);
       else
-        fwd_body<R, MODE, OP, 2, TileW>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+        fwd_body<R, MODE, OP, 2, TileW>(a, zblock, (int)blockIdx.z, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
                                         sKc, sGc);
     } else {
       // strips left / right of the rectangle lie in its y range: PML along x only
-      fwd_body<R, MODE, OP, 1, TileT>(a, zblock, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
+      fwd_body<R, MODE, OP, 1, TileT>(a, zblock, (int)blockIdx.z, tm, rhs, f.x0, f.y0, f.rx1, f.ry1, bid, sX, sD, sY1, sTab, sRed,
                                       sKc, sGc);
     }
   } else {
     const unsigned bid = (unsigned)(tm.bid_offset + t + tm.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
     if constexpr (OP == OP_Q || PATH == 0) {
       const int x0 = tm.ox + t * TX, y0 = tm.oy + (int)blockIdx.y * TY;
-      fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+      fwd_body<R, MODE, OP, 0, TileSq>(a, zblock, (int)blockIdx.z, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
                                        sKc, sGc);
     } else {
       constexpr int GX = TileG::TXS, GY = TileG::TYS;
@@ -515,10 +516,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (PATH == 0 ? 4 : 2) : 1) 
       const bool plain = (x0 >= L.plain_lo[0]) && (x0 + GX - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
                          (y0 + GY - 1 <= L.plain_hi[1]);
       if (plain)
-        fwd_body<R, MODE, OP, 0, TileG>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+        fwd_body<R, MODE, OP, 0, TileG>(a, zblock, (int)blockIdx.z, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
                                         sKc, sGc);
       else
-        fwd_body<R, MODE, OP, 2, TileG>(a, zblock, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
+        fwd_body<R, MODE, OP, 2, TileG>(a, zblock, (int)blockIdx.z, tm, rhs, x0, y0, tm.rx1, tm.ry1, bid, sX, sD, sY1, sTab, sRed,
                                         sKc, sGc);
     }
   }
@@ -755,6 +756,256 @@ void launch_fwd_gather(const StencilCall<R>& c, int mode, int op, cudaStream_t s
 
 template void launch_fwd_gather<float>(const StencilCall<float>&, int, int, cudaStream_t);
 template void launch_fwd_gather<double>(const StencilCall<double>&, int, int, cudaStream_t);
+
+
+// ----------------------------------------------------------------------------
+// The bottom solve C_4h (Sec. 3.2) as one persistent cooperative kernel
+// ----------------------------------------------------------------------------
+// The s-step CA-GMRES of the 4h level is a chain of short, latency-bound
+// steps on an L2-resident grid: p_{k+1} = B J(p_k) for k < s (a two-sweep
+// Jacobi map and a B apply per step), the Gram matrix of p_0 .. p_s with the
+// normal-equation solve, and e = sum_k y_k J(p_k).  As separate launches each
+// step pays a launch and a ramp; here every block of one cooperative launch
+// (all blocks resident) takes work items of each sweep in turn and waits at a
+// grid barrier between dependent steps.  The sweeps run the same tile bodies
+// as the separate launches (the 16 x 16 whole-grid tiles of small grids).
+//
+// Grid barrier: arrival counter bar[0] (never reset inside a launch) and
+// released generation bar[1], both zeroed before the launch; the last block
+// to arrive at barrier g releases generation g + 1.  Every wait is bounded:
+// after b.spins polls (about a second by default) the block records the
+// failure in *err and goes on (its results are then wrong, the host reports
+// HZ_ETIMEOUT, and no wait can hang the device).  b.extra > 0 (a test of that
+// path) makes the barrier expect arrivals that never come.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned& gen, int* err, unsigned spins, unsigned extra) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    const unsigned target = (gen + 1) * (gridDim.x + extra);
+    if (atomicAdd(bar, 1u) + 1u == target) {
+      atomicExch(bar + 1, gen + 1);
+    } else {
+      unsigned it = 0;
+      while (*reinterpret_cast<volatile unsigned*>(bar + 1) < gen + 1) {
+        if (++it > spins) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  ++gen;
+  __syncthreads();
+}
+
+// one sweep of the 4h operator over all work items (tile, z-block, right-hand side)
+template <class R, int MODE>
+__device__ __forceinline__ void bottom_sweep(const StencilCall<R>& c, const BottomArgs<R>& b, cx<R>* sX, cx<R>* sD,
+                                             cx<R>* sY1, const R* sTab, double* sRed, R (*sKc)[NT],
+                                             cx<R> (*sGc)[NT]) {
+  const LevelView<R>& L = c.lv;
+  TileMap tm;
+  tm.rx1 = L.nx - 1;
+  tm.ry1 = L.ny - 1;
+  const int items = b.ntx * b.nty * b.nzb * c.nrhs;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int rhs = it % c.nrhs, t = it / c.nrhs;
+    const int tx = t % b.ntx, r = t / b.ntx, ty = r % b.nty, bz = r / b.nty;
+    const int x0 = tx * TileG::TXS, y0 = ty * TileG::TYS;
+    const bool plain = (x0 >= L.plain_lo[0]) && (x0 + TileG::TXS - 1 <= L.plain_hi[0]) && (y0 >= L.plain_lo[1]) &&
+                       (y0 + TileG::TYS - 1 <= L.plain_hi[1]);
+    if (plain)
+      fwd_body<R, MODE, OP_AB, 0, TileG>(c, b.zblock, bz, tm, rhs, x0, y0, tm.rx1, tm.ry1, 0u, sX, sD, sY1, sTab,
+                                         sRed, sKc, sGc);
+    else
+      fwd_body<R, MODE, OP_AB, 2, TileG>(c, b.zblock, bz, tm, rhs, x0, y0, tm.rx1, tm.ry1, 0u, sX, sD, sY1, sTab,
+                                         sRed, sKc, sGc);
+    __syncthreads();  // the next item refills the plane ring
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_bottom4h(BottomArgs<R> b) {
+  constexpr int KN = kBottomSteps + 1, NV = KN * (KN + 1);  // Gram entries a <= b, re and im
+  constexpr int PL = TileSq::PLN;
+  __shared__ __align__(16) cx<R> sX[NSTAGE * PL];
+  __shared__ __align__(16) cx<R> sD[NSTAGE * PL];
+  __shared__ cx<R> sY1[PL];
+  __shared__ __align__(16) R sTab[kMaxSeg * kNumFn * 4];
+  __shared__ R sKc[NSTAGE][NT];
+  __shared__ cx<R> sGc[1][NT];
+  __shared__ double sRed[32];
+  __shared__ double sG[NT / 32][NV];
+  __shared__ double sres[NV];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5;
+  for (int i = tid; i < b.c.tab.nseg * kNumFn * 4; i += NT) sTab[i] = b.c.tab.coef[i];
+  __syncthreads();
+  unsigned gen = 0;
+  const int nrhs = b.c.nrhs;
+  const long long N = b.c.lv.N;
+  // basis: p_{k+1} = B J(p_k)
+  for (int k = 0; k < kBottomSteps; ++k) {
+    StencilCall<R> cj = b.c;
+    cj.x = b.P + k * b.vs;
+    cj.y = b.Zc + k * b.vs;
+    cj.base = nullptr;
+    bottom_sweep<R, M_J2>(cj, b, sX, sD, sY1, sTab, sRed, sKc, sGc);
+    grid_barrier(b.bar, gen, b.err, b.spins, b.extra);
+    StencilCall<R> ca = b.c;
+    ca.x = b.Zc + k * b.vs;
+    ca.y = b.P + (k + 1) * b.vs;
+    bottom_sweep<R, M_APPLY>(ca, b, sX, sD, sY1, sTab, sRed, sKc, sGc);
+    grid_barrier(b.bar, gen, b.err, b.spins, b.extra);
+  }
+  // Gram entries <p_a, p_b> (a <= b) per right-hand side: per-block partial sums
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+    R acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0;
+    const cx<R>* Pr = b.P + (long long)rhs * N;
+    for (long long i = blockIdx.x * (long long)NT + tid; i < N; i += (long long)gridDim.x * NT) {
+      cx<R> p[KN];
+#pragma unroll
+      for (int a = 0; a < KN; ++a) p[a] = Pr[a * b.vs + i];
+      int q = 0;
+#pragma unroll
+      for (int a = 0; a < KN; ++a)
+#pragma unroll
+        for (int c2 = a; c2 < KN; ++c2) {
+          const cx<R> t = cjmul(p[a], p[c2]);
+          acc[2 * q] += t.x;
+          acc[2 * q + 1] += t.y;
+          ++q;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double x = warp_sum((double)acc[v]);
+      if (lane == 0) sG[w][v] = x;
+    }
+    __syncthreads();
+    if (tid < NV) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < NT / 32; ++k) t += sG[k][tid];
+      b.partial[((size_t)blockIdx.x * nrhs + rhs) * NV + tid] = t;
+    }
+    __syncthreads();
+  }
+  grid_barrier(b.bar, gen, b.err, b.spins, b.extra);
+  // one block per right-hand side: sum the partials in block order, solve for y
+  for (int rhs = blockIdx.x; rhs < nrhs; rhs += gridDim.x) {
+    if (tid < NV) {
+      double t = 0.0;
+      for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(b.partial + ((size_t)k * nrhs + rhs) * NV + tid);
+      sres[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) gram_lsq_solve<KN>(sres, b.y + (size_t)rhs * b.ld * 2);
+    __syncthreads();
+  }
+  grid_barrier(b.bar, gen, b.err, b.spins, b.extra);
+  // e = sum_k y_k J(p_k)
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+    cx<R> yk[kBottomSteps];
+#pragma unroll
+    for (int k = 0; k < kBottomSteps; ++k) {
+      const double* yr = b.y + (size_t)rhs * b.ld * 2;
+      yk[k] = mkc<R>((R)__ldcg(yr + 2 * k), (R)__ldcg(yr + 2 * k + 1));
+    }
+    for (long long i = blockIdx.x * (long long)NT + tid; i < N; i += (long long)gridDim.x * NT) {
+      cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+      for (int k = 0; k < kBottomSteps; ++k) acc += yk[k] * b.Zc[k * b.vs + (long long)rhs * N + i];
+      b.e[(long long)rhs * N + i] = acc;
+    }
+  }
+}
+
+__global__ void k_coop_probe(int* p) {
+  if (p && blockIdx.x == 0 && threadIdx.x == 0) *p = 1;
+}
+
+// Cooperative launches captured into a CUDA graph (the preconditioner is
+// replayed as one graph): probed once per process on a trivial kernel.
+bool coop_capture_supported() {
+  static int cached = -1;
+  if (cached >= 0) return cached == 1;
+  int dev = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  bool ok = coop != 0;
+  if (ok) {
+    cudaStream_t s = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ex = nullptr;
+      int* nullp = nullptr;
+      void* args[] = {&nullp};
+      ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool launched = cudaLaunchCooperativeKernel((void*)k_coop_probe, dim3(1), dim3(32), args, 0, s) ==
+                              cudaSuccess;
+        const bool ended = cudaStreamEndCapture(s, &g) == cudaSuccess;
+        ok = launched && ended && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+      }
+      if (ex) cudaGraphExecDestroy(ex);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(s);
+    }
+    cudaGetLastError();  // clear any error of a refused capture
+  }
+  cached = ok ? 1 : 0;
+  return ok;
+}
+
+// Blocks of one cooperative launch of k_bottom4h<R> that fit on the device at once.
+template <class R>
+int bottom_max_blocks() {
+  static int cached[2] = {-1, -1};
+  int& c = cached[sizeof(R) == 8];
+  if (c < 0) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bottom4h<R>, NT, 0);
+    c = per * nsm;
+  }
+  return c;
+}
+
+template <class R>
+size_t bottom_partial_doubles(int nrhs) {
+  return (size_t)bottom_max_blocks<R>() * nrhs * (kBottomSteps + 1) * (kBottomSteps + 2);
+}
+
+template <class R>
+bool launch_bottom4h(BottomArgs<R> b, cudaStream_t s) {
+  const int maxb = bottom_max_blocks<R>();
+  if (maxb < 1) return false;
+  const LevelView<R>& L = b.c.lv;
+  b.ntx = (L.nx + TileG::TXS - 1) / TileG::TXS;
+  b.nty = (L.ny + TileG::TYS - 1) / TileG::TYS;
+  // z-blocks: about one work item per resident block, at most 64 planes each
+  const int tiles = b.ntx * b.nty * b.c.nrhs;
+  const int want = std::max(1, maxb / std::max(1, tiles));
+  b.zblock = std::min(64, std::max(2, (L.nz + want - 1) / want));
+  b.nzb = (L.nz + b.zblock - 1) / b.zblock;
+  const int grid = std::min(maxb, tiles * b.nzb);
+  if (cudaMemsetAsync(b.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return false;
+  void* args[] = {&b};
+  count_launch();
+  return cudaLaunchCooperativeKernel((void*)k_bottom4h<R>, dim3(grid), dim3(TX, TY), args, 0, s) == cudaSuccess;
+}
+
+template bool launch_bottom4h<float>(BottomArgs<float>, cudaStream_t);
+template bool launch_bottom4h<double>(BottomArgs<double>, cudaStream_t);
+template size_t bottom_partial_doubles<float>(int);
+template size_t bottom_partial_doubles<double>(int);
 
 }  // namespace gather
 }  // namespace hz

@@ -99,6 +99,32 @@ long long gather_blocks_per_rhs(int nx, int ny, int nz, const int* plain_lo, con
                                 int zblock, int zblock_f);
 long long replay_gather_layout(int nx, int ny, int nz, const int* plo, const int* phi, int op, int nrhs, int zblock,
                                int zblock_f, unsigned char* counts, long long* blocks);
+// The bottom solve C_4h (s-step CA-GMRES with kBottomSteps steps, two-sweep
+// Jacobi maps of B_4h) as one persistent cooperative kernel.
+constexpr int kBottomSteps = 4;
+template <class R>
+struct BottomArgs {
+  StencilCall<R> c;         // level 2, B shift, omega_4h, 1/diag of B_4h; x and y are set per sweep
+  cx<R>* P = nullptr;       // basis p_0 .. p_s (p_0 given), right-hand sides of one vector contiguous
+  cx<R>* Zc = nullptr;      // J(p_0) .. J(p_{s-1})
+  long long vs = 0;         // elements per basis vector (N_4h * nrhs)
+  cx<R>* e = nullptr;       // result sum_k y_k J(p_k)
+  double* y = nullptr;      // [nrhs][ld] complex coefficients (out)
+  int ld = kBottomSteps + 1;
+  double* partial = nullptr;  // bottom_partial_doubles(nrhs) Gram partial sums
+  unsigned* bar = nullptr;    // two counters, zeroed by the launcher
+  int* err = nullptr;         // set nonzero when a grid-barrier wait gave up
+  unsigned spins = 1u << 23;  // polls (100 ns apart) before a barrier wait gives up
+  unsigned extra = 0;         // > 0 only to test that path: arrivals the barrier waits for in vain
+  int zblock = 0, ntx = 0, nty = 0, nzb = 0;  // set by the launcher
+};
+// Enqueue on s; false when it could not be launched (nothing enqueued then
+// except, possibly, the barrier reset).
+template <class R>
+bool launch_bottom4h(BottomArgs<R> b, cudaStream_t s);
+template <class R>
+size_t bottom_partial_doubles(int nrhs);
+bool coop_capture_supported();
 }  // namespace gather
 
 // Grid transfers (Eq. full-weighting, Eq. linear-prolongation).

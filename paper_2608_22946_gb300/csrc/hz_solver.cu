@@ -162,6 +162,14 @@ struct hz_handle {
   std::map<std::tuple<int, int, int, const void*, void*>, std::pair<cudaGraphExec_t, unsigned long long>> graphs;
   double t_setup = 0;
   bool use_graphs = true;
+  // the bottom solve C_4h as one persistent cooperative kernel (forward, m_4h = 4,
+  // two Jacobi sweeps); its grid-barrier counters, error flag and Gram partials
+  bool coop_bottom = false;
+  unsigned* bot_bar = nullptr;
+  int* bot_err = nullptr;
+  double* bot_partial_f = nullptr;
+  double* bot_partial_d = nullptr;
+  unsigned bot_spins = 1u << 23, bot_extra = 0;
 };
 
 namespace {
@@ -576,6 +584,33 @@ void bottom_4h(hz_handle* H, bool adj, cx<R>* e, int nrhs) {
   const hz_params& p = H->p;
   const long long vs = H->lev[2].N * nrhs;
   const int s = p.m_4h;
+  // the persistent form where launch latency dominates: 4h grids below 2^20 nodes
+  // (larger ones keep the tuned rectangle/frame launches)
+  if (H->coop_bottom && !adj && s == gather::kBottomSteps && p.nJ_4h == 2 && H->lev[2].N < (1LL << 20)) {
+    gather::BottomArgs<R> b;
+    b.c = call<R>(H, 2, true, nrhs);
+    b.c.omega_j = (R)p.w_4h;
+    b.c.dinv = Sel<R>::dinv(H->lev[2], true);
+    HZ_REQUIRE(b.c.dinv, "internal: Jacobi diagonal of B_4h was not prepared");
+    b.P = W.P;
+    b.Zc = W.Zc;
+    b.vs = vs;
+    b.e = e;
+    b.y = W.yc;
+    b.ld = s + 1;
+    b.partial = sizeof(R) == 4 ? H->bot_partial_f : H->bot_partial_d;
+    b.bar = H->bot_bar;
+    b.err = H->bot_err;
+    b.spins = H->bot_spins;
+    b.extra = H->bot_extra;
+    if (!gather::launch_bottom4h<R>(b, H->st)) {
+      H->coop_bottom = false;
+      cudaGetLastError();
+      throw Fail{HZ_ECUDA, "cooperative launch of the persistent bottom solve failed (disabled for this handle)"};
+    }
+    HZ_LAUNCHED();
+    return;
+  }
   for (int k = 0; k < s; ++k) {
     jacobi<R>(H, 2, true, adj, W.P + k * vs, W.Zc + k * vs, p.nJ_4h, p.w_4h, nrhs);
     apply<R>(H, 2, true, adj, W.Zc + k * vs, W.P + (k + 1) * vs, nrhs);
@@ -1398,6 +1433,21 @@ SolveOut solve_c128(hz_handle* H, const cx<double>* b, cx<double>* x, int nrhs, 
   return o;
 }
 
+// A grid-barrier wait of the persistent bottom solve that gave up sets a
+// device flag (the kernel then finishes without waiting, its results
+// invalid); the synchronous entry points read and clear it.
+void check_bottom_err(hz_handle* H) {
+  if (!H->bot_err) return;
+  int e = 0;
+  HZ_CK(cudaMemcpyAsync(&e, H->bot_err, sizeof(int), cudaMemcpyDeviceToHost, H->st));
+  HZ_CK(cudaStreamSynchronize(H->st));
+  if (e) {
+    HZ_CK(cudaMemsetAsync(H->bot_err, 0, sizeof(int), H->st));
+    HZ_CK(cudaStreamSynchronize(H->st));
+    throw Fail{HZ_ETIMEOUT, "a grid-barrier wait of the persistent bottom solve gave up; the results are invalid"};
+  }
+}
+
 void upload_source_list(hz_handle* H, const hz_source* src, int ns) {
   std::vector<int> idx(3 * ns);
   std::vector<double> amp(2 * ns);
@@ -1559,6 +1609,22 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     auto t0 = std::chrono::steady_clock::now();
     plan_all(H, false);
     HZ_CK(cudaMemsetAsync(H->red_count, 0, sizeof(unsigned) * max_nrhs, H->st));
+    {
+      const char* np = std::getenv("HZ_NO_PERSISTENT");
+      H->coop_bottom = !(np && np[0] == '1') && gather::coop_capture_supported();
+      const char* bt = std::getenv("HZ_BARRIER_TEST");  // makes every grid-barrier wait run out (tests)
+      if (bt && bt[0] == '1') {
+        H->bot_extra = 1;
+        H->bot_spins = 4096;
+      }
+      if (H->coop_bottom) {
+        H->bot_bar = H->al.get<unsigned>(2);
+        H->bot_err = H->al.get<int>(1);
+        H->bot_partial_f = H->al.get<double>(gather::bottom_partial_doubles<float>(max_nrhs));
+        H->bot_partial_d = H->al.get<double>(gather::bottom_partial_doubles<double>(max_nrhs));
+        HZ_CK(cudaMemsetAsync(H->bot_err, 0, sizeof(int), H->st));
+      }
+    }
     std::vector<double> coef;
     double ds;
     build_table(table_host, table_rows, coef, ds);
@@ -1786,7 +1852,13 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
       const int ns = std::min(H->max_nrhs, nsrc - s0);
       source_rhs(H, src + s0, ns, H->b128);  // b = Q_h f (Eq. iofd-complete-system)
       cx<double>* v = (cx<double>*)v_dev + (size_t)s0 * N;
-      SolveOut o = solve_c128(H, H->b128, v, ns, false);
+      SolveOut o;
+      try {
+        o = solve_c128(H, H->b128, v, ns, false);
+      } catch (const Fail& f) {
+        if (f.st == HZ_ENONFINITE) check_bottom_err(H);  // a barrier that gave up explains the NaN
+        throw;
+      }
       tot.pc += o.pc;
       tot.passes += o.passes;
       tot.rel = std::max(tot.rel, o.rel);
@@ -1804,6 +1876,7 @@ hz_status helmholtz_solve(hz_handle* H, const hz_source* src, int nsrc, void* v_
       }
     }
     HZ_CK(cudaStreamSynchronize(H->st));
+    check_bottom_err(H);
     if (stats) {
       stats->pc_calls = tot.pc;
       stats->refine_passes = tot.passes;
@@ -1902,6 +1975,7 @@ hz_status helmholtz_adjoint_grad(hz_handle* H, const hz_source* src, int nsrc, c
     launch_fold_pml(H->g_ext, grad_dev, L0.nx, L0.ny, L0.nz, L0.n_pml, H->st);
     HZ_LAUNCHED();
     HZ_CK(cudaStreamSynchronize(H->st));
+    check_bottom_err(H);
     *misfit = J;
     if (stats) {
       stats->pc_calls = tot.pc;

@@ -7,6 +7,7 @@ applies to relative L2 <= 1e-5 (single-precision stencil and coefficients);
 solves to relative L2 <= 1e-6 against the oracle's converged solution.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -425,4 +426,71 @@ def test_block_solve_with_a_repeated_source_falls_back(hz):
     vref, _ = _oracle_solution(prob, [src[0], src[2]], tol=1e-11)
     for k, ref in ((0, vref[0]), (1, vref[0]), (2, vref[1])):
         assert rel_l2(v[k].cpu().numpy(), ref) <= 1e-6, k
+    s.close()
+
+
+# ------------------------------------------------------- persistent bottom solve
+def _launches_of(hz, f):
+    before = hz.kernel_launches()
+    f()
+    torch.cuda.synchronize()
+    return hz.kernel_launches() - before
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_persistent_bottom_solve_equals_the_launch_chain(hz, monkeypatch, prec):
+    """Algorithm 1 with C_4h as one persistent cooperative kernel (grid barriers
+    between the Jacobi, apply, Gram and combine steps) against the same
+    preconditioner with C_4h as a chain of launches (HZ_NO_PERSISTENT=1), and
+    both against the oracle; the persistent handle launches fewer kernels."""
+    w = W.layered_inclusion(n=40, n_pml=8, nsrc=2)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    params = hz.default_params(precision=hz.HZ_C128 if prec == "c128" else hz.HZ_C64)
+    prob, sp = make_pair(hz, w, params=params, max_nrhs=2)
+    monkeypatch.setenv("HZ_NO_PERSISTENT", "1")
+    sc = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
+    monkeypatch.delenv("HZ_NO_PERSISTENT")
+    r = W.random_complex((2,) + prob.levels[0].shape, 17)
+    rd = to_dev(r, dt)
+    zp = sp.threegrid_precond(rd).cpu().numpy()
+    zc = sc.threegrid_precond(rd).cpu().numpy()
+    tol = 1e-10 if prec == "c128" else 1e-4
+    assert rel_l2(zp, zc) <= tol, rel_l2(zp, zc)
+    M = tg.ThreeGrid(prob)
+    for k in range(2):
+        assert rel_l2(zp[k], M(r[k])) <= (1e-9 if prec == "c128" else 2e-4)
+    os.environ["HZ_NO_GRAPH"] = "1"
+    try:
+        sp2 = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
+        monkeypatch.setenv("HZ_NO_PERSISTENT", "1")
+        sc2 = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
+        monkeypatch.delenv("HZ_NO_PERSISTENT")
+    finally:
+        del os.environ["HZ_NO_GRAPH"]
+    n_p = _launches_of(hz, lambda: sp2.threegrid_precond(rd))
+    n_c = _launches_of(hz, lambda: sc2.threegrid_precond(rd))
+    assert n_c - n_p == 20 * 9, (n_p, n_c)   # 20 bottom solves, 10 launches each become one
+    for s in (sp, sc, sp2, sc2):
+        s.close()
+
+
+def test_persistent_bottom_barrier_timeout_is_reported(hz, monkeypatch):
+    """HZ_BARRIER_TEST=1 makes every grid-barrier wait of the persistent bottom
+    kernel wait for an arrival that never comes: each wait gives up after its
+    bounded poll count, the kernel finishes, the solve returns HZ_ETIMEOUT, and
+    the context stays usable (a new handle then solves correctly)."""
+    w = W.gaussian_lens(n=20, n_pml=4)
+    params = hz.default_params(tol=1e-9, max_pc=2)
+    monkeypatch.setenv("HZ_BARRIER_TEST", "1")
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=1)
+    monkeypatch.delenv("HZ_BARRIER_TEST")
+    with pytest.raises(hz.HzError) as e:
+        s.helmholtz_solve(w.sources)
+    assert e.value.status == hz.HZ_ETIMEOUT, e.value
+    s.close()
+    prob, s = make_pair(hz, w, params=hz.default_params(tol=1e-9))
+    v, _, st = s.helmholtz_solve(w.sources, want_u=False)
+    assert st["rel_res"] <= 1e-9
+    vref, _ = _oracle_solution(prob, w.sources, tol=1e-11)
+    assert rel_l2(v.cpu().numpy(), vref) <= 1e-6
     s.close()
