@@ -46,8 +46,9 @@ typedef enum {
   HZ_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
   HZ_ENOCONV = 4,     /* max_pc reached before the tolerance (results are filled) */
   HZ_ETIMEOUT = 5,    /* a bounded device wait gave up: a grid barrier of the persistent
-                         bottom-solve kernel (all of whose blocks are co-resident by a
-                         cooperative launch) did not release within about a second.  The
+                         bottom-solve kernel (opt-in: environment HZ_PERSISTENT=1 when the
+                         handle is created; all its blocks are co-resident by a cooperative
+                         launch) did not release within about a second.  The
                          kernel finishes without waiting, its results are invalid, and the
                          next helmholtz_solve or helmholtz_adjoint_grad on the handle
                          returns this status (threegrid_precond, being asynchronous, does

@@ -163,7 +163,8 @@ struct hz_handle {
   double t_setup = 0;
   bool use_graphs = true;
   // the bottom solve C_4h as one persistent cooperative kernel (forward, m_4h = 4,
-  // two Jacobi sweeps); its grid-barrier counters, error flag and Gram partials
+  // two Jacobi sweeps; opt-in through HZ_PERSISTENT=1 at creation); its
+  // grid-barrier counters, error flag and Gram partials
   bool coop_bottom = false;
   unsigned* bot_bar = nullptr;
   int* bot_err = nullptr;
@@ -1610,8 +1611,10 @@ hz_status hz_create(const hz_grid* grid, const double* c_dev, const hz_params* p
     plan_all(H, false);
     HZ_CK(cudaMemsetAsync(H->red_count, 0, sizeof(unsigned) * max_nrhs, H->st));
     {
-      const char* np = std::getenv("HZ_NO_PERSISTENT");
-      H->coop_bottom = !(np && np[0] == '1') && gather::coop_capture_supported();
+      // opt-in: on the 289^3 benchmark the ten grid barriers cost more than the
+      // launch gaps they replace (15.0 against 14.2-14.5 ms per preconditioner call)
+      const char* pp = std::getenv("HZ_PERSISTENT");
+      H->coop_bottom = (pp && pp[0] == '1') && gather::coop_capture_supported();
       const char* bt = std::getenv("HZ_BARRIER_TEST");  // makes every grid-barrier wait run out (tests)
       if (bt && bt[0] == '1') {
         H->bot_extra = 1;

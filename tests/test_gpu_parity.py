@@ -439,17 +439,17 @@ def _launches_of(hz, f):
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_persistent_bottom_solve_equals_the_launch_chain(hz, monkeypatch, prec):
-    """Algorithm 1 with C_4h as one persistent cooperative kernel (grid barriers
-    between the Jacobi, apply, Gram and combine steps) against the same
-    preconditioner with C_4h as a chain of launches (HZ_NO_PERSISTENT=1), and
+    """Algorithm 1 with C_4h as one persistent cooperative kernel (HZ_PERSISTENT=1:
+    grid barriers between the Jacobi, apply, Gram and combine steps) against
+    the same preconditioner with C_4h as a chain of launches (the default), and
     both against the oracle; the persistent handle launches fewer kernels."""
     w = W.layered_inclusion(n=40, n_pml=8, nsrc=2)
     dt = torch.complex128 if prec == "c128" else torch.complex64
     params = hz.default_params(precision=hz.HZ_C128 if prec == "c128" else hz.HZ_C64)
+    monkeypatch.setenv("HZ_PERSISTENT", "1")
     prob, sp = make_pair(hz, w, params=params, max_nrhs=2)
-    monkeypatch.setenv("HZ_NO_PERSISTENT", "1")
+    monkeypatch.delenv("HZ_PERSISTENT")
     sc = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
-    monkeypatch.delenv("HZ_NO_PERSISTENT")
     r = W.random_complex((2,) + prob.levels[0].shape, 17)
     rd = to_dev(r, dt)
     zp = sp.threegrid_precond(rd).cpu().numpy()
@@ -461,10 +461,10 @@ def test_persistent_bottom_solve_equals_the_launch_chain(hz, monkeypatch, prec):
         assert rel_l2(zp[k], M(r[k])) <= (1e-9 if prec == "c128" else 2e-4)
     os.environ["HZ_NO_GRAPH"] = "1"
     try:
+        monkeypatch.setenv("HZ_PERSISTENT", "1")
         sp2 = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
-        monkeypatch.setenv("HZ_NO_PERSISTENT", "1")
+        monkeypatch.delenv("HZ_PERSISTENT")
         sc2 = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=2)
-        monkeypatch.delenv("HZ_NO_PERSISTENT")
     finally:
         del os.environ["HZ_NO_GRAPH"]
     n_p = _launches_of(hz, lambda: sp2.threegrid_precond(rd))
@@ -475,15 +475,17 @@ def test_persistent_bottom_solve_equals_the_launch_chain(hz, monkeypatch, prec):
 
 
 def test_persistent_bottom_barrier_timeout_is_reported(hz, monkeypatch):
-    """HZ_BARRIER_TEST=1 makes every grid-barrier wait of the persistent bottom
-    kernel wait for an arrival that never comes: each wait gives up after its
+    """With the persistent bottom kernel (HZ_PERSISTENT=1), HZ_BARRIER_TEST=1
+    makes every grid-barrier wait wait for an arrival that never comes: each wait gives up after its
     bounded poll count, the kernel finishes, the solve returns HZ_ETIMEOUT, and
     the context stays usable (a new handle then solves correctly)."""
     w = W.gaussian_lens(n=20, n_pml=4)
     params = hz.default_params(tol=1e-9, max_pc=2)
+    monkeypatch.setenv("HZ_PERSISTENT", "1")
     monkeypatch.setenv("HZ_BARRIER_TEST", "1")
     s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, params=params, max_nrhs=1)
     monkeypatch.delenv("HZ_BARRIER_TEST")
+    monkeypatch.delenv("HZ_PERSISTENT")
     with pytest.raises(hz.HzError) as e:
         s.helmholtz_solve(w.sources)
     assert e.value.status == hz.HZ_ETIMEOUT, e.value
