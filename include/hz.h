@@ -196,6 +196,18 @@ hz_status iofd_coeffs(hz_handle* h, int level, double* kappa_dev, double* shell_
 hz_status iofd_apply(hz_handle* h, int level, int op, int precision, const void* x_dev, void* y_dev, int nrhs,
                      void* stream);
 
+/* One brick of a z-slab decomposition of the fine level (the brick-and-halo
+ * form of the paper's multi-GPU runs, Sec. 6.1): rows z0 .. z1-1 of y = Op x
+ * on level 0, from the brick's planes and a one-plane halo on each side.
+ *   op          HZ_OP_A or HZ_OP_B.
+ *   x_win_dev   DEVICE, (z1 - z0 + 2) planes of nx*ny values per right-hand side:
+ *               input planes z0-1 .. z1 (a halo plane outside 0 .. nz-1 is never
+ *               read; the zero boundary applies there).
+ *   y_win_dev   DEVICE, (z1 - z0) planes per right-hand side: output rows z0 .. z1-1.
+ *   0 <= z0 < z1 <= nz.  Each row takes the same arithmetic as in iofd_apply. */
+hz_status iofd_apply_window(hz_handle* h, int op, int precision, const void* x_win_dev, void* y_win_dev, int nrhs,
+                            int z0, int z1, void* stream);
+
 /* y = J_nsweeps(H, g; omega): the weighted Jacobi map from zero of
  * Eq. jacobi-map, the smoother inside S_h (level 0, H = A_h) and inside the
  * shifted cycle V_2h^sigma and the bottom solve C_4h (levels 1 and 2, H =

@@ -25,7 +25,7 @@ _STATUS = {0: "HZ_OK", 1: "HZ_EINVAL", 2: "HZ_ENOMEM", 3: "HZ_ECUDA", 4: "HZ_ENO
 EXPORTED = ["hz_default_params", "hz_create", "hz_destroy", "hz_last_error", "hz_workspace_bytes",
             "hz_set_params", "iofd_coeffs", "iofd_apply", "threegrid_precond", "helmholtz_solve",
             "helmholtz_adjoint_grad", "hz_kernel_launches", "iofd_residual_static", "hz_layout_check",
-            "iofd_jacobi"]
+            "iofd_jacobi", "iofd_apply_window"]
 
 
 class HzGrid(ctypes.Structure):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hz_kernel_launches.restype = ctypes.c_ulonglong
     lib.iofd_coeffs.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.iofd_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
+    lib.iofd_apply_window.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      vp]
     lib.iofd_jacobi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp,
                                 ctypes.c_int, vp]
     lib.iofd_residual_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
@@ -211,6 +213,25 @@ class Solver:
         _check_field(y, x.dtype, n * nrhs, "out")
         self._ok(self._lib.iofd_apply(self._h, level, op, prec, ctypes.c_void_p(x.data_ptr()),
                                       ctypes.c_void_p(y.data_ptr()), nrhs, _stream_ptr(stream)))
+        return y
+
+    def iofd_apply_window(self, x_win, z0, z1, op=HZ_OP_A, out=None, stream=None):
+        """Rows z0 .. z1-1 of Op x on the fine level from a brick with a one-plane
+        halo: x_win holds planes z0-1 .. z1 ((z1 - z0 + 2) planes per right-hand
+        side), the result (z1 - z0) planes per right-hand side."""
+        import torch
+        prec = HZ_C64 if x_win.dtype == torch.complex64 else HZ_C128
+        nz = self.level_shape[0][0]
+        if not (0 <= z0 < z1 <= nz):
+            raise ValueError(f"need 0 <= z0 < z1 <= {nz}")
+        plane = self.level_shape[0][1] * self.level_shape[0][2]
+        nrhs = _nrhs(x_win, (z1 - z0 + 2) * plane, "x_win")
+        _check_field(x_win, x_win.dtype, (z1 - z0 + 2) * plane * nrhs, "x_win")
+        y = (torch.empty((nrhs, z1 - z0) + self.level_shape[0][1:], dtype=x_win.dtype, device=x_win.device)
+             if out is None else out)
+        _check_field(y, x_win.dtype, (z1 - z0) * plane * nrhs, "out")
+        self._ok(self._lib.iofd_apply_window(self._h, op, prec, ctypes.c_void_p(x_win.data_ptr()),
+                                             ctypes.c_void_p(y.data_ptr()), nrhs, z0, z1, _stream_ptr(stream)))
         return y
 
     # -- iofd_jacobi -----------------------------------------------------------

@@ -50,12 +50,15 @@ struct FwdPlan {
   }
 };
 
-inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* phi, bool ab, int zb, int zbf) {
+// nzr: rows of a z-window (0: all nz); the tile set stays that of the whole grid
+inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* phi, bool ab, int zb, int zbf,
+                           int nzr = 0) {
   FwdPlan p;
-  p.zb = std::min(std::min(zb, kMaxZb), nz);
-  p.nzb = (nz + p.zb - 1) / p.zb;
-  p.zbf = std::min(std::min(zbf > 0 ? zbf : zb, kMaxZb), nz);
-  p.nzbf = (nz + p.zbf - 1) / p.zbf;
+  const int nzw = nzr > 0 ? nzr : nz;
+  p.zb = std::min(std::min(zb, kMaxZb), nzw);
+  p.nzb = (nzw + p.zb - 1) / p.zb;
+  p.zbf = std::min(std::min(zbf > 0 ? zbf : zb, kMaxZb), nzw);
+  p.nzbf = (nzw + p.zbf - 1) / p.zbf;
   p.ss = tile_set(nx, ny, nz);
   TileMap& f = p.frame;
   f.rw = rect_w(p.ss);
@@ -98,7 +101,14 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
 template <class R>
 inline FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, bool ab) {
   const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, nrhs);
-  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f);
+  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f, 0);
+}
+template <class R>
+inline FwdPlan plan_fwd(const StencilCall<R>& c, bool ab) {
+  const LevelView<R>& L = c.lv;
+  const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
+  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f,
+                     c.zr1 > 0 ? c.zr1 - c.zr0 : 0);
 }
 
 template <class R, int MODE, int OPK, int RB, int SS>
@@ -122,7 +132,7 @@ void launch_fwd_ss(const StencilCall<R>& c, const FwdPlan& p, cudaStream_t s) {
 
 template <class R, int MODE, int OPK, int RB>
 void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
-  const FwdPlan p = plan_fwd(c.lv, c.nrhs, OPK != OPK_Q);
+  const FwdPlan p = plan_fwd(c, OPK != OPK_Q);
   if constexpr (OPK != OPK_Q) {
     if (p.fused) {
       TileMap tm = p.frame;

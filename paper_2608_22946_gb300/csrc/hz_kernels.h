@@ -46,6 +46,12 @@ struct StencilCall {
   // on it beside the rectangle launch (fork / join through the two events)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // z-window of a fine-level APPLY (one brick of a z-slab decomposition): rows
+  // [zr0, zr1) are computed (zr1 = 0: all nz rows); input plane q is read at
+  // x + rhs * xstride + (q - xz0) * plane, output row z written at
+  // y + rhs * ystride + (z - zr0) * plane (strides 0: N)
+  int zr0 = 0, zr1 = 0, xz0 = 0;
+  long long xstride = 0, ystride = 0;
 };
 
 template <class R>

@@ -1789,6 +1789,49 @@ hz_status iofd_apply(hz_handle* H, int level, int op, int precision, const void*
   });
 }
 
+hz_status iofd_apply_window(hz_handle* H, int op, int precision, const void* x, void* y, int nrhs, int z0, int z1,
+                            void* stream) {
+  if (!H) return HZ_EINVAL;
+  return run_guarded(H, [&] {
+    HZ_REQUIRE(op == HZ_OP_A || op == HZ_OP_B, "the window apply takes HZ_OP_A or HZ_OP_B");
+    HZ_REQUIRE(x && y && x != y, "x and y must be distinct non-null device pointers");
+    HZ_REQUIRE(nrhs >= 1 && nrhs <= H->max_nrhs, "nrhs out of range");
+    HZ_REQUIRE(precision == HZ_C64 || precision == HZ_C128, "precision must be HZ_C64 or HZ_C128");
+    const Level& L0 = H->lev[0];
+    HZ_REQUIRE(z0 >= 0 && z0 < z1 && z1 <= L0.nz, "need 0 <= z0 < z1 <= nz (fine-level planes)");
+    const long long plane = (long long)L0.nx * L0.ny;
+    auto fill = [&](auto& c) {
+      c.zr0 = z0;
+      c.zr1 = z1;
+      c.xz0 = z0 - 1;
+      c.xstride = (long long)(z1 - z0 + 2) * plane;
+      c.ystride = (long long)(z1 - z0) * plane;
+    };
+    cudaStream_t old = H->st;
+    H->st = (cudaStream_t)stream;
+    try {
+      if (precision == HZ_C64) {
+        StencilCall<float> c = call<float>(H, 0, op == HZ_OP_B, nrhs);
+        c.x = (const cx<float>*)x;
+        c.y = (cx<float>*)y;
+        fill(c);
+        launch_stencil<float>(c, M_APPLY, OP_AB, false, H->st);
+      } else {
+        StencilCall<double> c = call<double>(H, 0, op == HZ_OP_B, nrhs);
+        c.x = (const cx<double>*)x;
+        c.y = (cx<double>*)y;
+        fill(c);
+        launch_stencil<double>(c, M_APPLY, OP_AB, false, H->st);
+      }
+      HZ_LAUNCHED();
+    } catch (...) {
+      H->st = old;
+      throw;
+    }
+    H->st = old;
+  });
+}
+
 hz_status iofd_jacobi(hz_handle* H, int level, int op, int precision, int nsweeps, double omega, const void* g,
                       void* y, int nrhs, void* stream) {
   if (!H) return HZ_EINVAL;

@@ -76,6 +76,7 @@ def test_null_handle_is_rejected(lib):
     assert lib.helmholtz_solve(None, None, 0, None, None, None) == 1
     assert lib.helmholtz_adjoint_grad(None, None, 0, None, 0, None, None, None, None) == 1
     assert lib.iofd_residual_static(None, 0, 0, 0, None, None, None, None, 1, None) == 1
+    assert lib.iofd_apply_window(None, 0, 0, None, None, 1, 0, 1, None) == 1
     assert lib.hz_workspace_bytes(None, ctypes.byref(p), 1, None) == 1
     g = hz.HzGrid(48, 48, 48, 8, 1 / 32, 1.0, 1.1)
     assert lib.hz_create(ctypes.byref(g), None, ctypes.byref(p), None, 17, 1, None, None) == 1

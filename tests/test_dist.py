@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 def test_two_rank_max_time_and_aggregate():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
@@ -197,7 +197,7 @@ def test_two_ranks_split_the_sources_and_sum_the_gradient(monkeypatch):
         monkeypatch.setenv(var, "1")
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_grad_worker, args=(world, port, out), nprocs=world, join=True)
     w = W.random_field(n=20, n_pml=4, nsrc=4, nrec_side=3)

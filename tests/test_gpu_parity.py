@@ -496,3 +496,34 @@ def test_persistent_bottom_barrier_timeout_is_reported(hz, monkeypatch):
     vref, _ = _oracle_solution(prob, w.sources, tol=1e-11)
     assert rel_l2(v.cpu().numpy(), vref) <= 1e-6
     s.close()
+
+
+# ------------------------------------------------------ z-slab brick emulation
+@pytest.mark.parametrize("n,n_pml", [(40, 8), (104, 8), (208, 16)])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_window_apply_emulates_z_slab_bricks(hz, n, n_pml, prec):
+    """The fine-level operator applied brick by brick from a one-plane halo
+    (iofd_apply_window, the per-rank step of the z-slab sharding) gives the rows
+    of the whole-grid apply: three uneven bricks, A and B, two right-hand
+    sides, on grids that take each fine-level tile set (one fused launch,
+    coarse-shaped and fine-shaped rectangle/frame launches)."""
+    from paper_2608_22946_gb300 import sharding
+    w = W.gaussian_lens(n=n, n_pml=n_pml)
+    s = hz.Solver(w.n, w.n_pml, w.h, w.omega, w.c, max_nrhs=2)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    x = to_dev(W.random_complex((2,) + s.level_shape[0], 41), dt)
+    nz = s.level_shape[0][0]
+    for op in (hz.HZ_OP_A, hz.HZ_OP_B):
+        y = s.iofd_apply(x, op=op, level=0)
+        scale = float(y.abs().max())
+        for rank in range(3):
+            z0, z1 = sharding.slab(nz, 3, rank)
+            win = torch.zeros((2, z1 - z0 + 2) + s.level_shape[0][1:], dtype=dt, device="cuda")
+            lo, hi = max(z0 - 1, 0), min(z1 + 1, nz)
+            win[:, lo - (z0 - 1):hi - (z0 - 1)] = x[:, lo:hi]
+            yb = s.iofd_apply_window(win, z0, z1, op=op)
+            err = float((yb - y[:, z0:z1]).abs().max()) / scale
+            assert err <= (1e-13 if prec == "c128" else 1e-6), (n, op, rank, err)
+    with pytest.raises(ValueError):
+        s.iofd_apply_window(win, 3, 3)
+    s.close()
