@@ -392,9 +392,12 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   const int tid = threadIdx.x;
   const int tx = tid % TS::TXT, ty = tid / TS::TXT;
   const int nx = Lv.nx, ny = Lv.ny, nz = Lv.nz;
-  const int zr1 = a.zr1 > 0 ? a.zr1 : nz;
-  const int zb0 = a.zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, zr1);
-  const long long xs = a.xstride > 0 ? a.xstride : Lv.N, ys = a.ystride > 0 ? a.ystride : Lv.N;
+  // row window (z-slab brick) of an APPLY; other modes always cover all rows
+  constexpr bool WIN = MODE == M_APPLY;
+  const int zr0 = WIN ? a.zr0 : 0, xz0 = WIN ? a.xz0 : 0;
+  const int zr1 = (WIN && a.zr1 > 0) ? a.zr1 : nz;
+  const int zb0 = zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, zr1);
+  const long long xs = (WIN && a.xstride > 0) ? a.xstride : Lv.N, ys = (WIN && a.ystride > 0) ? a.ystride : Lv.N;
   const int nplanes = zb1 - zb0 + 2;
   const int plane_sz = nx * ny;
   const long long N = Lv.N;
@@ -466,7 +469,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
     const int zo = zin ? q * plane_sz : 0;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const cx<R>* Xr = a.x + (size_t)(rhs0 + r) * (size_t)xs + (zin ? zo - (long long)a.xz0 * plane_sz : 0);
+      const cx<R>* Xr = a.x + (size_t)(rhs0 + r) * (size_t)xs + (zin ? zo - (long long)xz0 * plane_sz : 0);
       cx<R>* dst = sX + ((size_t)st * RB + r) * PLN + tid;
 #pragma unroll
       for (int j = 0; j < NSLOT; ++j)
@@ -676,7 +679,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
               const cx<R> d0 = a.dinv[idx];
               out = x0c + om * (d0 * (gq[r][i] - h));
             }
-            a.y[(size_t)(rhs0 + r) * (size_t)ys + idx - (long long)a.zr0 * plane_sz] = out;
+            a.y[(size_t)(rhs0 + r) * (size_t)ys + idx - (long long)zr0 * plane_sz] = out;
           }
         }
         if (o0) accP[r][i] += contrib<0, CORR, ZP>(C[CP][i], T0[i], c, e, kk, Ac, Bc, zq0, ez0);
@@ -729,10 +732,12 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
 }
 
 // does any output row of z-block blockIdx.z (of the call's row window) lie in the z-PML?
-template <class R>
+template <int MODE, class R>
 __device__ __forceinline__ bool block_in_zpml(const StencilCall<R>& a, int zblock) {
   const LevelView<R>& L = a.lv;
-  const int zb0 = a.zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, a.zr1 > 0 ? a.zr1 : L.nz);
+  constexpr bool WIN = MODE == M_APPLY;
+  const int zr0 = WIN ? a.zr0 : 0, zr1 = (WIN && a.zr1 > 0) ? a.zr1 : L.nz;
+  const int zb0 = zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, zr1);
   return zb0 < L.plain_lo[2] || zb1 - 1 > L.plain_hi[2];
 }
 
@@ -757,7 +762,7 @@ __global__ void __launch_bounds__(Shapes<SS>::Rect::NT,
   const unsigned bid = (unsigned)(tm.bid_offset + t + tm.ntx * (blockIdx.y + gridDim.y * blockIdx.z));
   const int x0 = tm.ox + t * ShRect::TWN, y0 = tm.oy + (int)blockIdx.y * ShRect::TYT;
   const unsigned nb = (unsigned)tm.nblk_total;
-  if (block_in_zpml(a, zblock))
+  if (block_in_zpml<MODE>(a, zblock))
     fwd_tile<R, MODE, OPK, 0, true, ShRect, RB>(a, fsm, zblock, x0, y0, tm.rx1, tm.ry1, g * RB, bid, nb);
   else
     fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, tm.rx1, tm.ry1, g * RB, bid, nb);
@@ -777,7 +782,7 @@ __global__ void __launch_bounds__(Shapes<SS>::Wide::NT, FMinB<R, RB, Shapes<SS>:
   const FrameTile f = decode_frame(tm, t);
   const unsigned bid = (unsigned)(tm.bid_offset + t + tm.count * blockIdx.z);
   const unsigned nb = (unsigned)tm.nblk_total;
-  const bool zp = block_in_zpml(a, zblock);
+  const bool zp = block_in_zpml<MODE>(a, zblock);
   if (f.wide) {
     if (zp) fwd_tile<R, MODE, OPK, 3, true, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
     else fwd_tile<R, MODE, OPK, 3, false, ShWide, RB>(a, fsm, zblock, f.x0, f.y0, f.rx1, f.ry1, g * RB, bid, nb);
@@ -803,7 +808,7 @@ __global__ void __launch_bounds__(Shapes<SS>::Rect::NT, sizeof(R) == 8 ? 1 : 2) 
   if constexpr (OPK == OPK_Q) {
     fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
   } else {
-    const bool zp = block_in_zpml(a, zblock);
+    const bool zp = block_in_zpml<MODE>(a, zblock);
     if (grid_tile_form(x0, y0, ShRect::TWN, ShRect::TYT, a.lv.nx, a.lv.ny, a.lv.plain_lo, a.lv.plain_hi) == 0) {
       if (zp) fwd_tile<R, MODE, OPK, 0, true, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
       else fwd_tile<R, MODE, OPK, 0, false, ShRect, RB>(a, fsm, zblock, x0, y0, rx1, ry1, g * RB, bid, nb);
@@ -827,7 +832,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2) k_fwd_fused(Stenc
   const int nrect = tm.ntx * tm.nrow;
   const unsigned bid = (unsigned)(t + (nrect + tm.count) * blockIdx.z);
   const unsigned nb = (unsigned)tm.nblk_total;
-  const bool zp = block_in_zpml(a, zblock);
+  const bool zp = block_in_zpml<MODE>(a, zblock);
   if (t < nrect) {
     const int x0 = tm.px0 + (t % tm.ntx) * SRect::TWN, y0 = tm.py0 + (t / tm.ntx) * SRect::TYT;
     if (zp) fwd_tile<R, MODE, OPK, 0, true, SRect, RB>(a, fsm, zblock, x0, y0, tm.px1, tm.py1, g * RB, bid, nb);

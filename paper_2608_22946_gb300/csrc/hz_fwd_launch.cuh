@@ -110,6 +110,12 @@ inline FwdPlan plan_fwd(const StencilCall<R>& c, bool ab) {
   return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f,
                      c.zr1 > 0 ? c.zr1 - c.zr0 : 0);
 }
+// (the row window applies to APPLY launches only: other modes plan all rows)
+template <class R, int MODE>
+inline FwdPlan plan_fwd_mode(StencilCall<R> c, bool ab) {
+  if (MODE != M_APPLY) c.zr0 = c.zr1 = 0;
+  return plan_fwd(c, ab);
+}
 
 template <class R, int MODE, int OPK, int RB, int SS>
 void launch_fwd_split(const StencilCall<R>& c, const FwdPlan& p, int ng, int nblk_total, cudaStream_t s);
@@ -132,7 +138,7 @@ void launch_fwd_ss(const StencilCall<R>& c, const FwdPlan& p, cudaStream_t s) {
 
 template <class R, int MODE, int OPK, int RB>
 void launch_fwd_rb(const StencilCall<R>& c, cudaStream_t s) {
-  const FwdPlan p = plan_fwd(c, OPK != OPK_Q);
+  const FwdPlan p = plan_fwd_mode<R, MODE>(c, OPK != OPK_Q);
   if constexpr (OPK != OPK_Q) {
     if (p.fused) {
       TileMap tm = p.frame;
