@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libhz.so")
 # per (precision, mode) part so that its kernels build in parallel
 SOURCES = [("hz_stencil.cu", [], "hz_stencil.o"), ("hz_vec.cu", [], "hz_vec.o"), ("hz_solver.cu", [], "hz_solver.o"),
            ("hz_fwd_gather.cu", [], "hz_fwd_gather.o"), ("hz_block.cu", [], "hz_block.o")] + [
-    ("hz_fwd.cu", [f"-DHZ_FWD_PART={k}"], f"hz_fwd_{k}.o") for k in range(5)]
+    ("hz_fwd.cu", [f"-DHZ_FWD_PART={k}"], f"hz_fwd_{k}.o") for k in range(6)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -1,10 +1,10 @@
 // Explicit instantiations of the forward stencil (hz_fwd.cuh), split by
 // (precision, mode) so that the build compiles the parts in parallel: this
-// file is compiled once per part with -DHZ_FWD_PART=0..4.
+// file is compiled once per part with -DHZ_FWD_PART=0..5.
 #include "hz_fwd_launch.cuh"
 
 #ifndef HZ_FWD_PART
-#error "compile with -DHZ_FWD_PART=<0..4>"
+#error "compile with -DHZ_FWD_PART=<0..5>"
 #endif
 
 namespace hz {
@@ -26,6 +26,9 @@ HZ_FWD_INST(double, M_APPLY)
 HZ_FWD_INST(double, M_RESID)
 HZ_FWD_INST(double, M_J2)
 HZ_FWD_INST(double, M_JSWEEP)
+#elif HZ_FWD_PART == 5
+HZ_FWD_INST(float, M_AWIN)
+HZ_FWD_INST(double, M_AWIN)
 #endif
 
 #undef HZ_FWD_INST

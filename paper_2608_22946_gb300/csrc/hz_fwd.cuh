@@ -392,8 +392,8 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
   const int tid = threadIdx.x;
   const int tx = tid % TS::TXT, ty = tid / TS::TXT;
   const int nx = Lv.nx, ny = Lv.ny, nz = Lv.nz;
-  // row window (z-slab brick) of an APPLY; other modes always cover all rows
-  constexpr bool WIN = MODE == M_APPLY;
+  // row window (z-slab brick): M_AWIN only; every other mode covers all rows
+  constexpr bool WIN = MODE == M_AWIN;
   const int zr0 = WIN ? a.zr0 : 0, xz0 = WIN ? a.xz0 : 0;
   const int zr1 = (WIN && a.zr1 > 0) ? a.zr1 : nz;
   const int zb0 = zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, zr1);
@@ -664,7 +664,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
           if (act[i]) {
             const int idx = (p - 1) * plane_sz + col0 + i;
             cx<R> out;
-            if constexpr (MODE == M_APPLY) {
+            if constexpr (MODE == M_APPLY || MODE == M_AWIN) {
               out = h;
             } else if constexpr (MODE == M_RESID) {
               out = gq[r][i] - h;
@@ -735,7 +735,7 @@ __device__ __forceinline__ void fwd_tile(const StencilCall<R>& a, unsigned char*
 template <int MODE, class R>
 __device__ __forceinline__ bool block_in_zpml(const StencilCall<R>& a, int zblock) {
   const LevelView<R>& L = a.lv;
-  constexpr bool WIN = MODE == M_APPLY;
+  constexpr bool WIN = MODE == M_AWIN;
   const int zr0 = WIN ? a.zr0 : 0, zr1 = (WIN && a.zr1 > 0) ? a.zr1 : L.nz;
   const int zb0 = zr0 + blockIdx.z * zblock, zb1 = min(zb0 + zblock, zr1);
   return zb0 < L.plain_lo[2] || zb1 - 1 > L.plain_hi[2];

@@ -110,10 +110,10 @@ inline FwdPlan plan_fwd(const StencilCall<R>& c, bool ab) {
   return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f,
                      c.zr1 > 0 ? c.zr1 - c.zr0 : 0);
 }
-// (the row window applies to APPLY launches only: other modes plan all rows)
+// (the row window applies to M_AWIN launches only: other modes plan all rows)
 template <class R, int MODE>
 inline FwdPlan plan_fwd_mode(StencilCall<R> c, bool ab) {
-  if (MODE != M_APPLY) c.zr0 = c.zr1 = 0;
+  if (MODE != M_AWIN) c.zr0 = c.zr1 = 0;
   return plan_fwd(c, ab);
 }
 

@@ -15,7 +15,8 @@ namespace hz {
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-enum StencilMode { M_APPLY = 0, M_RESID = 1, M_J2 = 2, M_JSWEEP = 3, M_J1 = 4 };
+// M_AWIN: an APPLY of the fine level from a z-window (StencilCall::zr0 .. xstride)
+enum StencilMode { M_APPLY = 0, M_RESID = 1, M_J2 = 2, M_JSWEEP = 3, M_J1 = 4, M_AWIN = 5 };
 enum StencilOp { OP_AB = 0, OP_Q = 1 };
 
 // Reduction target of a kernel that finishes with a deterministic

@@ -1815,13 +1815,13 @@ hz_status iofd_apply_window(hz_handle* H, int op, int precision, const void* x, 
         c.x = (const cx<float>*)x;
         c.y = (cx<float>*)y;
         fill(c);
-        launch_stencil<float>(c, M_APPLY, OP_AB, false, H->st);
+        launch_stencil<float>(c, M_AWIN, OP_AB, false, H->st);
       } else {
         StencilCall<double> c = call<double>(H, 0, op == HZ_OP_B, nrhs);
         c.x = (const cx<double>*)x;
         c.y = (cx<double>*)y;
         fill(c);
-        launch_stencil<double>(c, M_APPLY, OP_AB, false, H->st);
+        launch_stencil<double>(c, M_AWIN, OP_AB, false, H->st);
       }
       HZ_LAUNCHED();
     } catch (...) {

@@ -33,6 +33,8 @@ extern template void launch_fwd<double, M_APPLY>(const StencilCall<double>&, int
 extern template void launch_fwd<double, M_RESID>(const StencilCall<double>&, int, cudaStream_t);
 extern template void launch_fwd<double, M_J2>(const StencilCall<double>&, int, cudaStream_t);
 extern template void launch_fwd<double, M_JSWEEP>(const StencilCall<double>&, int, cudaStream_t);
+extern template void launch_fwd<float, M_AWIN>(const StencilCall<float>&, int, cudaStream_t);
+extern template void launch_fwd<double, M_AWIN>(const StencilCall<double>&, int, cudaStream_t);
 extern template void fwd_init_attrs<float, M_APPLY>();
 extern template void fwd_init_attrs<float, M_RESID>();
 extern template void fwd_init_attrs<float, M_J2>();
@@ -41,6 +43,8 @@ extern template void fwd_init_attrs<double, M_APPLY>();
 extern template void fwd_init_attrs<double, M_RESID>();
 extern template void fwd_init_attrs<double, M_J2>();
 extern template void fwd_init_attrs<double, M_JSWEEP>();
+extern template void fwd_init_attrs<float, M_AWIN>();
+extern template void fwd_init_attrs<double, M_AWIN>();
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int PW = TX + 2, PH = TY + 2, PLANE = PW * PH;
@@ -298,6 +302,7 @@ void launch_stencil(const StencilCall<R>& c, int mode, int op, bool adjoint, cud
       case M_RESID: launch_fwd<R, M_RESID>(c, opk, s); break;
       case M_J2: launch_fwd<R, M_J2>(c, opk, s); break;
       case M_JSWEEP: launch_fwd<R, M_JSWEEP>(c, opk, s); break;
+      case M_AWIN: launch_fwd<R, M_AWIN>(c, opk, s); break;
     }
   } else {
     if (op == OP_Q) {
@@ -464,6 +469,8 @@ void init_kernel_attributes() {
   fwd_init_attrs<double, M_RESID>();
   fwd_init_attrs<double, M_J2>();
   fwd_init_attrs<double, M_JSWEEP>();
+  fwd_init_attrs<float, M_AWIN>();
+  fwd_init_attrs<double, M_AWIN>();
 }
 
 template void launch_stencil<float>(const StencilCall<float>&, int, int, bool, cudaStream_t);
