@@ -99,11 +99,6 @@ inline FwdPlan plan_layout(int nx, int ny, int nz, const int* plo, const int* ph
 }
 
 template <class R>
-inline FwdPlan plan_fwd(const LevelView<R>& L, int nrhs, bool ab) {
-  const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, nrhs);
-  return plan_layout(L.nx, L.ny, L.nz, L.plain_lo, L.plain_hi, ab, zb, L.zblock_f, 0);
-}
-template <class R>
 inline FwdPlan plan_fwd(const StencilCall<R>& c, bool ab) {
   const LevelView<R>& L = c.lv;
   const int zb = L.zblock > 0 ? L.zblock : choose_zblock(L.nx, L.ny, L.nz, c.nrhs);
