@@ -929,13 +929,18 @@ __global__ void k_coop_probe(int* p) {
   if (p && blockIdx.x == 0 && threadIdx.x == 0) *p = 1;
 }
 
+// per-device caches of the probes below (every thread that races on a first
+// probe stores the same answer)
+constexpr int kProbeDevices = 64;
+
 // Cooperative launches captured into a CUDA graph (the preconditioner is
-// replayed as one graph): probed once per process on a trivial kernel.
+// replayed as one graph): probed once per process and device on a trivial kernel.
 bool coop_capture_supported() {
-  static int cached = -1;
-  if (cached >= 0) return cached == 1;
+  static int cache[kProbeDevices];  // 0 unknown, 1 yes, 2 no
   int dev = 0, coop = 0;
   cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kProbeDevices) return false;
+  if (cache[dev]) return cache[dev] == 1;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   bool ok = coop != 0;
   if (ok) {
@@ -959,23 +964,24 @@ bool coop_capture_supported() {
     }
     cudaGetLastError();  // clear any error of a refused capture
   }
-  cached = ok ? 1 : 0;
+  cache[dev] = ok ? 1 : 2;
   return ok;
 }
 
 // Blocks of one cooperative launch of k_bottom4h<R> that fit on the device at once.
 template <class R>
 int bottom_max_blocks() {
-  static int cached[2] = {-1, -1};
-  int& c = cached[sizeof(R) == 8];
-  if (c < 0) {
-    int dev = 0, nsm = 0, per = 0;
-    cudaGetDevice(&dev);
+  static int cache[kProbeDevices];  // 0 unknown, else blocks + 1
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kProbeDevices) return 0;
+  if (!cache[dev]) {
+    int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bottom4h<R>, NT, 0);
-    c = per * nsm;
+    cache[dev] = per * nsm + 1;
   }
-  return c;
+  return cache[dev] - 1;
 }
 
 template <class R>
